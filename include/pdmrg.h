@@ -1,0 +1,228 @@
+/*
+ * pdmrg.h -- C ABI of the GB300 two-site DMRG engine (libpdmrg.so).
+ *
+ * The engine implements the serial two-site DMRG step and the real-space parallel scheme of
+ * Stoudenmire & White, "Real-Space Parallel Density Matrix Renormalization Group":
+ *   - the wavefunction on a bond, Sec. II Eq. (wf), optimised by Davidson with the
+ *     Hamiltonian projected into the |a>|s1>|s2>|c> basis (Sec. II);
+ *   - the SVD Psi = A Lambda B with truncation to the m largest singular values, Sec. II
+ *     Eq. (svd), followed by the gauge move (A Lambda or Lambda B) and the transformation of
+ *     the projected operators (Sec. II, operator-transformation paragraph);
+ *   - the Lambda V Lambda split with V = Lambda^{-1} (Eqs. inverse, isvd), the merge
+ *     Psi' = psi'_3 V psi'_4 (Eq. merge), the staggered sweep of Fig. 4, and the accurate
+ *     recursive SVD of the Appendix at shared bonds.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Charges are integers (2*S^z, or all zero for a model without U(1) symmetry).  A bond is a
+ *    list of sectors (q, m) with strictly ascending q.
+ *  * MPO tensor W_j: row-major [D_j][d][d][D_{j+1}], W_j[w][s][s'][w'] = <s|op|s'>; every MPO
+ *    channel w carries a flux f(w) and W_j[w][s][s'][w'] != 0 requires
+ *    qn[s] - qn[s'] = f(w') - f(w).
+ *  * Packed block layouts (all FP64, row-major inside a block, blocks back to back):
+ *      site tensor  blocks (left sector i, local state s), i ascending then s ascending,
+ *                   present when q_i + qn[s] is a sector of the right bond; block [m_i][m_r].
+ *      two-site psi blocks (i, s1, s2) in that lexicographic order, present when
+ *                   q_i + qn[s1] + qn[s2] is a sector of the right bond; block [m_i][m_c].
+ *      environment  blocks (bra sector i, MPO channel w), i then w ascending, present when
+ *                   q_i - f(w) is a sector of the same bond; block [m_i][m_ket].  Left
+ *                   environments hold the projected operators of the left block (sites
+ *                   0..j-1), right ones those of the right block.
+ *  * Every function returns a dmrg_status and never aborts, throws or traps.  Device-side
+ *    failures (capacity, non-finite values, a bounded wait that ran out) are recorded in a
+ *    device error word and returned by the call that observes them.
+ *  * Pointers named *_dev are device pointers owned by the caller; *_host are host pointers
+ *    owned by the caller.  Inputs are read, never retained after the call returns.
+ *  * `stream` arguments are cudaStream_t values (NULL = legacy default stream); calls are
+ *    stream-ordered and return after the work is enqueued unless stated otherwise.
+ */
+#ifndef PDMRG_H
+#define PDMRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DMRG_OK = 0,
+    DMRG_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, inconsistent charges) */
+    DMRG_ERR_CUDA = 2,      /* a CUDA runtime call failed; see dmrg_last_error */
+    DMRG_ERR_OOM = 3,       /* device allocation failed */
+    DMRG_ERR_CAPACITY = 4,  /* a size exceeds a fixed capacity of the engine */
+    DMRG_ERR_QN = 5,        /* quantum-number bookkeeping inconsistency */
+    DMRG_ERR_NUMERIC = 6,   /* non-finite value or breakdown detected */
+    DMRG_ERR_TIMEOUT = 7,   /* a bounded device wait ran out (the kernel returned early) */
+    DMRG_ERR_STATE = 8      /* call not valid in the context's current state */
+} dmrg_status;
+
+/* Arithmetic of the large contractions (H_eff matvec and environment updates).  The
+ * Davidson Rayleigh-Ritz problem, re-orthogonalisation, SVD and Lambda^{-1} are FP64 in
+ * every mode. */
+typedef enum {
+    DMRG_FP64 = 0,          /* FP64 everywhere (parity mode)                                   */
+    DMRG_TF32 = 1,          /* tcgen05 kind::tf32, FP32 accumulate                             */
+    DMRG_BF16 = 2           /* tcgen05 kind::f16 (bf16 operands), FP32 accumulate              */
+} dmrg_precision;
+
+/* ------------------------------------------------------------------------------------------
+ * Problem description
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int n_sites;            /* L >= 2                                                         */
+    int d;                  /* local dimension, 2..4                                          */
+    const int* qn_local;    /* [d] charges of the local basis states                          */
+    const int* D;           /* [L+1] MPO bond dimensions, D[0] = D[L] = 1                     */
+    const int* flux;        /* [sum D] channel fluxes, bond 0 first                           */
+    const double* W;        /* concatenated W_j, j = 0..L-1, row-major [D_j][d][d][D_{j+1}]    */
+    int qn_total;           /* total charge of the state                                      */
+} dmrg_mpo_desc;
+
+typedef struct {
+    const int* n_sectors;   /* [L+1] sectors per bond (bond 0 = {0}, bond L = {qn_total})      */
+    const int* sector_q;    /* concatenated sector charges, bond 0 first                      */
+    const int* sector_m;    /* concatenated sector dimensions                                 */
+    const double* data;     /* concatenated packed site tensors, site 0 first                 */
+} dmrg_mps_desc;
+
+typedef struct {
+    int precision;          /* dmrg_precision                                                 */
+    int kmax;               /* Davidson subspace size before restart (2..32, default 8)       */
+    void* stream;           /* cudaStream_t base stream (region streams are forked from it)   */
+} dmrg_config;
+
+typedef struct {
+    int m_max;              /* kept states per bond (truncation target m)                     */
+    double dav_tol;         /* Davidson stops when |r| <= dav_tol * max(1, |theta|)           */
+    int dav_max_iter;       /* Davidson iteration cap per bond                                */
+} dmrg_sweep_params;
+
+typedef struct {
+    double energy;          /* Davidson energy of the sweep's last local problem (last merge
+                               with regions)                                                  */
+    double max_trunc_err;   /* largest discarded weight of the sweep                          */
+    int max_m;              /* largest bond dimension after truncation                        */
+    int n_matvec;           /* H_eff applications                                             */
+    int n_steps;            /* two-site steps (merges included)                               */
+    int dav_nonconv;        /* local problems that hit dav_max_iter                           */
+    double seconds;         /* host wall time of the call (synchronised)                      */
+    double matvec_seconds;  /* summed device time of the matvecs (CUDA events)                */
+    double matvec_flops;    /* algorithmic flops of those matvecs (nonzero blocks only)       */
+    double min_fidelity;    /* smallest merge fidelity 1-|<Psi'|Psi>| of the sweep (-1: none)  */
+    double max_fidelity;    /* largest merge fidelity of the sweep (-1: none)                 */
+} dmrg_sweep_stats;
+
+typedef struct dmrg_ctx dmrg_ctx;
+
+/* ------------------------------------------------------------------------------------------
+ * Context API
+ * ---------------------------------------------------------------------------------------- */
+
+/* Create a context for the Hamiltonian given as an MPO (the "projected operators" of Sec. II
+ * are built from it).  Copies the MPO to the device.  *out receives a context owned by the
+ * caller and released with dmrg_destroy.  Errors: DMRG_ERR_ARG on inconsistent sizes or a
+ * W entry that violates the flux rule. */
+dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_config* cfg);
+
+/* Load a matrix product state (packed layout above, host memory, copied), bring it to
+ * right-canonical form with the orthogonality centre on site 0 by untruncated SVDs from the
+ * right, normalise it, and build every right environment.  Serial mode afterwards. */
+dmrg_status dmrg_set_mps(dmrg_ctx* ctx, const dmrg_mps_desc* mps);
+
+/* Real-space parallel set-up (Sec. II, Fig. 4): split the chain into n_regions blocks at
+ * bonds round(k L / n_regions); run `warmup` serial sweeps (the last one's left half-sweep
+ * performs the Lambda V Lambda split at every boundary it crosses; warmup = 0 moves the
+ * gauge by untruncated SVDs instead), then move even regions (1-based) to their right end.
+ * Each region gets its own CUDA stream.  n_regions = 1 returns to serial mode. */
+dmrg_status dmrg_setup_regions(dmrg_ctx* ctx, int n_regions, int warmup,
+                               const dmrg_sweep_params* p);
+
+/* One sweep.  Serial mode: bonds 0..L-2 moving right, then L-2..0 moving left.  Region mode:
+ * Fig. 4 (a)-(d) with every region on its own stream, merges (Eq. merge) at the meeting
+ * boundaries after both regions arrived.  Blocks until the sweep is done.  stats may be NULL. */
+dmrg_status dmrg_sweep(dmrg_ctx* ctx, const dmrg_sweep_params* p, dmrg_sweep_stats* stats);
+
+/* Merge at region boundary k (1..n_regions-1): Psi' = psi'_3 V psi'_4 with the stored V
+ * (Eq. merge), normalisation, Davidson on the shared bond with the left environment of the
+ * left region and the right environment of the right region, accurate SVD (Appendix),
+ * new V = Lambda^{-1}, environment hand-off.  Both regions must sit at the boundary.
+ * fidelity_out (nullable) receives 1 - |<Psi'|Psi>|; energy_out (nullable) the energy. */
+dmrg_status dmrg_merge(dmrg_ctx* ctx, int k, const dmrg_sweep_params* p,
+                       double* fidelity_out, double* energy_out);
+
+/* FP64 Rayleigh quotient <psi|H_eff|psi>/<psi|psi> of the current two-site wavefunction
+ * (serial mode) -- the energy of the whole state when the environments are current. */
+dmrg_status dmrg_energy(dmrg_ctx* ctx, double* E_out);
+
+/* Sector table of bond b (0..L): writes up to cap entries, *n_out = number of sectors.
+ * In region mode the bond is read from the region that owns it. */
+dmrg_status dmrg_get_bond(dmrg_ctx* ctx, int b, int* q_out, int* m_out, int cap, int* n_out);
+
+/* Singular values stored for bond b by its last SVD (descending within each sector,
+ * sectors ascending, normalised to sum lambda^2 = 1).  *n_out = count. */
+dmrg_status dmrg_get_lambda(dmrg_ctx* ctx, int b, double* lam_out, int cap, int* n_out);
+
+/* Orthogonality-centre site of the serial state, or of region k in region mode. */
+dmrg_status dmrg_get_center(dmrg_ctx* ctx, int region, int* site_out);
+
+dmrg_status dmrg_destroy(dmrg_ctx* ctx);
+
+/* Message of the last failure on this context (context-owned, valid until the next call). */
+const char* dmrg_last_error(const dmrg_ctx* ctx);
+const char* dmrg_status_string(int status);
+
+/* ------------------------------------------------------------------------------------------
+ * Operation API: single steps on caller-provided device buffers (used for element-wise
+ * parity tests and micro-benchmarks).  Layouts are the packed layouts above.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int d;
+    const int* qn_local;    /* [d]                                                            */
+    int nl; const int* ql; const int* ml;   /* bond left of site 1  (sectors of psi's a)       */
+    int nr; const int* qr; const int* mr;   /* bond right of site 2 (sectors of psi's c)       */
+    int D0, D1, D2;         /* MPO bonds around the two sites                                 */
+    const int* f0; const int* f1; const int* f2;   /* their channel fluxes                    */
+    const double* W1;       /* [D0][d][d][D1] host                                            */
+    const double* W2;       /* [D1][d][d][D2] host                                            */
+} dmrg_bond_desc;
+
+/* y = H_eff x with H_eff = L x W1 x W2 x R (Sec. II projected Hamiltonian, written as
+ * out[a',s1,s2,c'] = sum L[a',w,a] W1[w,s1,s1',w'] W2[w',s2,s2',w''] R[c',w'',c] x[a,s1',s2',c]).
+ * L_dev, R_dev: packed environments of the left/right bond; x_dev, y_dev: packed two-site
+ * vectors (FP64).  prec selects the contraction arithmetic.  flops_out (nullable) receives
+ * the algorithmic flop count of one application. */
+dmrg_status dmrg_heff_apply(const dmrg_bond_desc* bd, int prec, const double* L_dev,
+                            const double* R_dev, const double* x_dev, double* y_dev,
+                            double* flops_out, void* stream);
+
+/* Left-environment update through one site (Sec. II operator transformation by A):
+ * Lout[b',w',b] = sum A[a',s,b'] Lin[a',w,a] W[w,s,s',w'] A[a,s',b].  Bonds: (nl,ql,ml) left
+ * of the site, (nr,qr,mr) right of it; D0/f0 and D1/f1 the MPO bonds, W1 the site's MPO
+ * tensor (D2, f2, W2 unused). */
+dmrg_status dmrg_env_left(const dmrg_bond_desc* bd, int prec, const double* Lin_dev,
+                          const double* A_dev, double* Lout_dev, void* stream);
+
+/* Right-environment update (operator transformation by B):
+ * Rout[a',w,a] = sum B[a',s,c'] Rin[c',w',c] W[w,s,s',w'] B[a,s',c]. */
+dmrg_status dmrg_env_right(const dmrg_bond_desc* bd, int prec, const double* Rin_dev,
+                           const double* B_dev, double* Rout_dev, void* stream);
+
+/* Two-site SVD with truncation (Eq. svd): psi (packed two-site) -> A (packed site tensor on
+ * the left bond x new middle bond), lambda, B (packed site tensor middle x right).  The kept
+ * set: lambda <= 1e-12 lambda_max dropped; order (lambda desc, q asc, index asc); first m_max
+ * kept; a degenerate group at the cut (relative gap <= 1e-10) dropped whole.  lambda is
+ * normalised to sum lambda^2 = 1.  accurate != 0 applies the Appendix recursion (eps 1e-4).
+ * Outputs: middle-bond sectors (nm_out, qm_out[cap], mm_out[cap]), A_dev/B_dev/lam_dev sized
+ * by the caller for the worst case (no truncation), trunc_out (nullable) the discarded weight.
+ * Synchronises the stream (the kept sector sizes are returned to the host). */
+dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int m_max,
+                           int accurate, double* A_dev, double* lam_dev, double* B_dev,
+                           int cap, int* nm_out, int* qm_out, int* mm_out, double* trunc_out,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDMRG_H */

@@ -1,0 +1,256 @@
+"""GB300-native two-site DMRG engine (real-space parallel DMRG, Stoudenmire & White).
+
+Thin ctypes binding over ``libpdmrg.so`` whose C ABI is declared in ``include/pdmrg.h``.
+This module only marshals arguments: every step of the DMRG hot path runs in the library's
+CUDA kernels.  Device buffers are passed as integer device pointers (e.g. ``tensor.data_ptr()``
+of a CUDA torch tensor); streams as integer ``cudaStream_t`` handles (0 = default stream).
+The library must be built first (``paper_1301_3494_gb300.build.build()``); importing the
+binding never falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdmrg.so")
+
+FP64, TF32, BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16}
+
+_ip = C.POINTER(C.c_int)
+_dp = C.POINTER(C.c_double)
+
+
+class MpoDesc(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("d", C.c_int), ("qn_local", _ip), ("D", _ip), ("flux", _ip),
+                ("W", _dp), ("qn_total", C.c_int)]
+
+
+class MpsDesc(C.Structure):
+    _fields_ = [("n_sectors", _ip), ("sector_q", _ip), ("sector_m", _ip), ("data", _dp)]
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p)]
+
+
+class SweepParams(C.Structure):
+    _fields_ = [("m_max", C.c_int), ("dav_tol", C.c_double), ("dav_max_iter", C.c_int)]
+
+
+class SweepStats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("max_trunc_err", C.c_double), ("max_m", C.c_int),
+                ("n_matvec", C.c_int), ("n_steps", C.c_int), ("dav_nonconv", C.c_int),
+                ("seconds", C.c_double), ("matvec_seconds", C.c_double), ("matvec_flops", C.c_double),
+                ("min_fidelity", C.c_double), ("max_fidelity", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BondDesc(C.Structure):
+    _fields_ = [("d", C.c_int), ("qn_local", _ip),
+                ("nl", C.c_int), ("ql", _ip), ("ml", _ip),
+                ("nr", C.c_int), ("qr", _ip), ("mr", _ip),
+                ("D0", C.c_int), ("D1", C.c_int), ("D2", C.c_int),
+                ("f0", _ip), ("f1", _ip), ("f2", _ip),
+                ("W1", _dp), ("W2", _dp)]
+
+
+class DMRGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)} ({status}): {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libpdmrg.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1301_3494_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, st = C.c_void_p, C.c_int
+        L.dmrg_status_string.restype = C.c_char_p
+        L.dmrg_status_string.argtypes = [C.c_int]
+        L.dmrg_last_error.restype = C.c_char_p
+        L.dmrg_last_error.argtypes = [vp]
+        L.dmrg_init_mpo.argtypes = [C.POINTER(vp), C.POINTER(MpoDesc), C.POINTER(Config)]
+        L.dmrg_set_mps.argtypes = [vp, C.POINTER(MpsDesc)]
+        L.dmrg_setup_regions.argtypes = [vp, C.c_int, C.c_int, C.POINTER(SweepParams)]
+        L.dmrg_sweep.argtypes = [vp, C.POINTER(SweepParams), C.POINTER(SweepStats)]
+        L.dmrg_merge.argtypes = [vp, C.c_int, C.POINTER(SweepParams), _dp, _dp]
+        L.dmrg_energy.argtypes = [vp, _dp]
+        L.dmrg_get_bond.argtypes = [vp, C.c_int, _ip, _ip, C.c_int, _ip]
+        L.dmrg_get_lambda.argtypes = [vp, C.c_int, _dp, C.c_int, _ip]
+        L.dmrg_get_center.argtypes = [vp, C.c_int, _ip]
+        L.dmrg_destroy.argtypes = [vp]
+        L.dmrg_heff_apply.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp, _dp, vp]
+        L.dmrg_env_left.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
+        L.dmrg_env_right.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
+        L.dmrg_svd_split.argtypes = [C.POINTER(BondDesc), vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, _ip, _ip, _ip,
+                                     _dp, vp]
+        for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_merge",
+                     "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_destroy",
+                     "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_svd_split"):
+            getattr(L, name).restype = st
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().dmrg_status_string(int(s)).decode()
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = lib().dmrg_last_error(ctx).decode()
+        raise DMRGError(status, msg)
+
+
+def _i32(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+
+
+def _f64(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+# ------------------------------------------------------------------------------------------
+# Operation-level entry points
+# ------------------------------------------------------------------------------------------
+class Bond:
+    """Host description of one two-site bond (keeps the arrays alive for the C struct)."""
+
+    def __init__(self, qn, left, right, W1, f0, f1, W2=None, f2=None):
+        self.qn = _i32(qn)
+        self.ql, self.ml = _i32(list(left.keys())), _i32(list(left.values()))
+        self.qr, self.mr = _i32(list(right.keys())), _i32(list(right.values()))
+        self.W1 = _f64(W1)
+        self.f0, self.f1 = _i32(f0), _i32(f1)
+        self.W2 = _f64(W2) if W2 is not None else _f64(np.zeros(1))
+        self.f2 = _i32(f2) if f2 is not None else _i32(np.zeros(1))
+        D0, _, _, D1 = self.W1.shape
+        D2 = self.W2.shape[3] if W2 is not None else 1
+        self.desc = BondDesc(len(self.qn), _ptr(self.qn, _ip), len(self.ql), _ptr(self.ql, _ip), _ptr(self.ml, _ip),
+                             len(self.qr), _ptr(self.qr, _ip), _ptr(self.mr, _ip), D0, D1, D2,
+                             _ptr(self.f0, _ip), _ptr(self.f1, _ip), _ptr(self.f2, _ip),
+                             _ptr(self.W1, _dp), _ptr(self.W2, _dp))
+
+
+def heff_apply(bond: Bond, prec, L_dev, R_dev, x_dev, y_dev, stream=0):
+    """y = H_eff x on device buffers; returns the algorithmic flop count."""
+    fl = C.c_double(0.0)
+    _check(lib().dmrg_heff_apply(C.byref(bond.desc), int(prec), L_dev, R_dev, x_dev, y_dev, C.byref(fl), stream))
+    return fl.value
+
+
+def env_left(bond: Bond, prec, Lin_dev, A_dev, Lout_dev, stream=0):
+    _check(lib().dmrg_env_left(C.byref(bond.desc), int(prec), Lin_dev, A_dev, Lout_dev, stream))
+
+
+def env_right(bond: Bond, prec, Rin_dev, B_dev, Rout_dev, stream=0):
+    _check(lib().dmrg_env_right(C.byref(bond.desc), int(prec), Rin_dev, B_dev, Rout_dev, stream))
+
+
+def svd_split(bond: Bond, psi_dev, m_max, accurate, A_dev, lam_dev, B_dev, cap=4096, stream=0):
+    """Returns (middle-bond sectors dict, discarded weight)."""
+    nm = C.c_int(0)
+    qm = np.zeros(cap, np.int32)
+    mm = np.zeros(cap, np.int32)
+    tr = C.c_double(0.0)
+    _check(lib().dmrg_svd_split(C.byref(bond.desc), psi_dev, int(m_max), int(bool(accurate)), A_dev, lam_dev, B_dev,
+                                cap, C.byref(nm), _ptr(qm, _ip), _ptr(mm, _ip), C.byref(tr), stream))
+    return {int(q): int(m) for q, m in zip(qm[: nm.value], mm[: nm.value])}, tr.value
+
+
+# ------------------------------------------------------------------------------------------
+# Context-level engine
+# ------------------------------------------------------------------------------------------
+class Engine:
+    """A DMRG state on the GPU: MPO, MPS, environments, optional real-space regions."""
+
+    def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0):
+        self._keep = [_f64(W), _i32(flux), _i32(D), _i32(qn)]
+        W_, f_, D_, q_ = self._keep
+        self.L = len(D_) - 1
+        self.qn = [int(x) for x in q_]
+        desc = MpoDesc(self.L, len(q_), _ptr(q_, _ip), _ptr(D_, _ip), _ptr(f_, _ip), _ptr(W_, _dp), int(qtot))
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg = Config(prec, int(kmax), C.c_void_p(stream))
+        h = C.c_void_p()
+        _check(lib().dmrg_init_mpo(C.byref(h), C.byref(desc), C.byref(cfg)))
+        self._h = h
+
+    @staticmethod
+    def params(m_max, dav_tol=1e-10, dav_max_iter=100):
+        return SweepParams(int(m_max), float(dav_tol), int(dav_max_iter))
+
+    def set_mps(self, bonds, site_data):
+        """bonds: list of L+1 dicts charge -> dim; site_data: concatenated packed site tensors."""
+        ns = _i32([len(b) for b in bonds])
+        sq = _i32([q for b in bonds for q in b.keys()])
+        sm = _i32([m for b in bonds for m in b.values()])
+        data = _f64(site_data)
+        desc = MpsDesc(_ptr(ns, _ip), _ptr(sq, _ip), _ptr(sm, _ip), _ptr(data, _dp))
+        _check(lib().dmrg_set_mps(self._h, C.byref(desc)), self._h)
+
+    def setup_regions(self, n_regions, warmup, m_max, dav_tol=1e-10, dav_max_iter=100):
+        p = self.params(m_max, dav_tol, dav_max_iter)
+        _check(lib().dmrg_setup_regions(self._h, int(n_regions), int(warmup), C.byref(p)), self._h)
+
+    def sweep(self, m_max, dav_tol=1e-10, dav_max_iter=100):
+        p = self.params(m_max, dav_tol, dav_max_iter)
+        s = SweepStats()
+        _check(lib().dmrg_sweep(self._h, C.byref(p), C.byref(s)), self._h)
+        return s.as_dict()
+
+    def merge(self, k, m_max, dav_tol=1e-10, dav_max_iter=100):
+        p = self.params(m_max, dav_tol, dav_max_iter)
+        f, e = C.c_double(0), C.c_double(0)
+        _check(lib().dmrg_merge(self._h, int(k), C.byref(p), C.byref(f), C.byref(e)), self._h)
+        return f.value, e.value
+
+    def energy(self):
+        e = C.c_double(0)
+        _check(lib().dmrg_energy(self._h, C.byref(e)), self._h)
+        return e.value
+
+    def bond(self, b):
+        q = np.zeros(8192, np.int32)
+        m = np.zeros(8192, np.int32)
+        n = C.c_int(0)
+        _check(lib().dmrg_get_bond(self._h, int(b), _ptr(q, _ip), _ptr(m, _ip), 8192, C.byref(n)), self._h)
+        return {int(a): int(b_) for a, b_ in zip(q[: n.value], m[: n.value])}
+
+    def lam(self, b):
+        v = np.zeros(65536)
+        n = C.c_int(0)
+        _check(lib().dmrg_get_lambda(self._h, int(b), _ptr(v, _dp), 65536, C.byref(n)), self._h)
+        return v[: n.value].copy()
+
+    def center(self, region=0):
+        s = C.c_int(0)
+        _check(lib().dmrg_get_center(self._h, int(region), C.byref(s)), self._h)
+        return s.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dmrg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,193 @@
+// C ABI: operation-level entry points (single steps on caller device buffers).
+#include <cstring>
+#include <memory>
+
+#include "plans.h"
+
+namespace pd {
+thread_local std::string g_last_error;
+
+Sec make_sec(int n, const int* q, const int* m) {
+    PD_REQUIRE(n >= 0 && (n == 0 || (q && m)), DMRG_ERR_ARG, "bad sector list");
+    Sec s;
+    for (int i = 0; i < n; ++i) {
+        PD_REQUIRE(m[i] > 0, DMRG_ERR_ARG, "sector dimension must be positive");
+        if (i) PD_REQUIRE(q[i] > q[i - 1], DMRG_ERR_ARG, "sector charges must ascend strictly");
+        s.q.push_back(q[i]);
+        s.m.push_back(m[i]);
+    }
+    return s;
+}
+
+SiteMPO make_site_mpo(int Dl, int Dr, int d, const int* fl, const int* fr, const double* W, const std::vector<int>& qn) {
+    PD_REQUIRE(Dl > 0 && Dr > 0 && d > 0 && fl && fr && W, DMRG_ERR_ARG, "bad MPO tensor description");
+    SiteMPO s;
+    s.Dl = Dl; s.Dr = Dr; s.d = d;
+    s.W.assign(W, W + (size_t)Dl * d * d * Dr);
+    s.fl.assign(fl, fl + Dl);
+    s.fr.assign(fr, fr + Dr);
+    for (int w = 0; w < Dl; ++w)
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b)
+                for (int wp = 0; wp < Dr; ++wp)
+                    if (s.at(w, a, b, wp) != 0.0)
+                        PD_REQUIRE(qn[a] - qn[b] == s.fr[wp] - s.fl[w], DMRG_ERR_QN,
+                                   "MPO element violates the flux rule q(s)-q(s') = f(w')-f(w)");
+    return s;
+}
+
+dmrg_status fail(const Error& e) {
+    g_last_error = e.msg;
+    return e.st;
+}
+
+void check_err_word(unsigned* err, cudaStream_t st) {
+    unsigned h = 0;
+    PD_CK(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    if (h & ERRBIT_TIMEOUT) throw Error{DMRG_ERR_TIMEOUT, "a bounded device wait ran out"};
+    if (h & ERRBIT_BOUNDS) throw Error{DMRG_ERR_CAPACITY, "a device index check failed"};
+    if (h & ERRBIT_NONFINITE) throw Error{DMRG_ERR_NUMERIC, "non-finite value detected"};
+}
+
+}  // namespace pd
+
+using namespace pd;
+
+namespace {
+struct BondCtx {
+    std::vector<int> qn;
+    Sec bl, br;
+    SiteMPO w1, w2;
+};
+
+BondCtx read_bond(const dmrg_bond_desc* bd, bool need_w2) {
+    PD_REQUIRE(bd && bd->d > 0 && bd->d <= 8 && bd->qn_local, DMRG_ERR_ARG, "bad bond descriptor");
+    BondCtx b;
+    b.qn.assign(bd->qn_local, bd->qn_local + bd->d);
+    b.bl = make_sec(bd->nl, bd->ql, bd->ml);
+    b.br = make_sec(bd->nr, bd->qr, bd->mr);
+    b.w1 = make_site_mpo(bd->D0, bd->D1, bd->d, bd->f0, bd->f1, bd->W1, b.qn);
+    if (need_w2) b.w2 = make_site_mpo(bd->D1, bd->D2, bd->d, bd->f1, bd->f2, bd->W2, b.qn);
+    return b;
+}
+
+bool valid_prec(int p) { return p == DMRG_FP64 || p == DMRG_TF32 || p == DMRG_BF16; }
+}  // namespace
+
+extern "C" {
+
+const char* dmrg_status_string(int s) {
+    switch (s) {
+        case DMRG_OK: return "ok";
+        case DMRG_ERR_ARG: return "invalid argument";
+        case DMRG_ERR_CUDA: return "CUDA error";
+        case DMRG_ERR_OOM: return "out of device memory";
+        case DMRG_ERR_CAPACITY: return "capacity exceeded";
+        case DMRG_ERR_QN: return "quantum-number inconsistency";
+        case DMRG_ERR_NUMERIC: return "numerical failure";
+        case DMRG_ERR_TIMEOUT: return "bounded device wait ran out";
+        case DMRG_ERR_STATE: return "invalid state";
+        default: return "unknown status";
+    }
+}
+
+dmrg_status dmrg_heff_apply(const dmrg_bond_desc* bd, int prec, const double* L_dev, const double* R_dev,
+                            const double* x_dev, double* y_dev, double* flops_out, void* stream) {
+    try {
+        PD_REQUIRE(valid_prec(prec), DMRG_ERR_ARG, "unknown precision");
+        PD_REQUIRE(L_dev && R_dev && x_dev && y_dev, DMRG_ERR_ARG, "null buffer");
+        cudaStream_t st = (cudaStream_t)stream;
+        BondCtx b = read_bond(bd, true);
+        TwoSiteMPO t = two_site_mpo(b.w1, b.w2);
+        EnvSlab L, R;
+        env_alloc(L, b.bl, b.w1.fl, prec, st);
+        env_from_packed(L, L_dev, st);
+        env_alloc(R, b.br, b.w2.fr, prec, st);
+        env_from_packed(R, R_dev, st);
+        env_make_operand(L, prec, st);
+        env_make_operand(R, prec, st);
+        auto plan = make_heff_plan(b.bl, b.br, b.qn, t, L.lay, R.lay, prec, st);
+        DBuf err;
+        err.ensure(4, st);
+        PD_CK(cudaMemsetAsync(err.p, 0, 4, st));
+        heff_apply(*plan, L, R, x_dev, y_dev, err.as<unsigned>(), st);
+        check_err_word(err.as<unsigned>(), st);
+        if (flops_out) *flops_out = plan->flops;
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    }
+}
+
+dmrg_status dmrg_env_left(const dmrg_bond_desc* bd, int prec, const double* Lin_dev, const double* A_dev,
+                          double* Lout_dev, void* stream) {
+    try {
+        PD_REQUIRE(valid_prec(prec), DMRG_ERR_ARG, "unknown precision");
+        PD_REQUIRE(Lin_dev && A_dev && Lout_dev, DMRG_ERR_ARG, "null buffer");
+        cudaStream_t st = (cudaStream_t)stream;
+        BondCtx b = read_bond(bd, false);
+        EnvSlab Li, Lo;
+        env_alloc(Li, b.bl, b.w1.fl, prec, st);
+        env_from_packed(Li, Lin_dev, st);
+        env_alloc(Lo, b.br, b.w1.fr, prec, st);
+        DBuf err;
+        err.ensure(4, st);
+        PD_CK(cudaMemsetAsync(err.p, 0, 4, st));
+        env_update_left(b.bl, b.br, b.qn, b.w1, Li, A_dev, Lo, prec, err.as<unsigned>(), st);
+        check_err_word(err.as<unsigned>(), st);
+        env_to_packed(Lo, Lout_dev, st);
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    }
+}
+
+dmrg_status dmrg_env_right(const dmrg_bond_desc* bd, int prec, const double* Rin_dev, const double* B_dev,
+                           double* Rout_dev, void* stream) {
+    try {
+        PD_REQUIRE(valid_prec(prec), DMRG_ERR_ARG, "unknown precision");
+        PD_REQUIRE(Rin_dev && B_dev && Rout_dev, DMRG_ERR_ARG, "null buffer");
+        cudaStream_t st = (cudaStream_t)stream;
+        BondCtx b = read_bond(bd, false);
+        EnvSlab Ri, Ro;
+        env_alloc(Ri, b.br, b.w1.fr, prec, st);
+        env_from_packed(Ri, Rin_dev, st);
+        env_alloc(Ro, b.bl, b.w1.fl, prec, st);
+        DBuf err;
+        err.ensure(4, st);
+        PD_CK(cudaMemsetAsync(err.p, 0, 4, st));
+        env_update_right(b.bl, b.br, b.qn, b.w1, Ri, B_dev, Ro, prec, err.as<unsigned>(), st);
+        check_err_word(err.as<unsigned>(), st);
+        env_to_packed(Ro, Rout_dev, st);
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    }
+}
+
+dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int m_max, int accurate, double* A_dev,
+                           double* lam_dev, double* B_dev, int cap, int* nm_out, int* qm_out, int* mm_out,
+                           double* trunc_out, void* stream) {
+    try {
+        PD_REQUIRE(bd && bd->d > 0 && bd->qn_local, DMRG_ERR_ARG, "bad bond descriptor");
+        PD_REQUIRE(psi_dev && A_dev && B_dev && lam_dev && nm_out && qm_out && mm_out, DMRG_ERR_ARG, "null buffer");
+        PD_REQUIRE(m_max >= 1, DMRG_ERR_ARG, "m_max must be >= 1");
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<int> qn(bd->qn_local, bd->qn_local + bd->d);
+        Sec bl = make_sec(bd->nl, bd->ql, bd->ml), br = make_sec(bd->nr, bd->qr, bd->mr);
+        SplitResult r = svd_split(bl, br, qn, qn, psi_dev, m_max, 1e-12, accurate != 0, 0, 0, A_dev, B_dev, lam_dev, st);
+        PD_REQUIRE(r.mid.n() <= cap, DMRG_ERR_CAPACITY, "output sector capacity too small");
+        *nm_out = r.mid.n();
+        for (int i = 0; i < r.mid.n(); ++i) {
+            qm_out[i] = r.mid.q[i];
+            mm_out[i] = r.mid.m[i];
+        }
+        if (trunc_out) *trunc_out = r.trunc;
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,775 @@
+// Stateful two-site DMRG engine behind the context C ABI: serial sweeps (Sec. II) and the
+// real-space parallel scheme (Sec. II Eqs. inverse/isvd/merge, Fig. 4) with one CUDA stream
+// per region on a single GPU.
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <thread>
+
+#include "plans.h"
+
+namespace pd {
+extern thread_local std::string g_last_error;
+Sec make_sec(int n, const int* q, const int* m);
+SiteMPO make_site_mpo(int Dl, int Dr, int d, const int* fl, const int* fr, const double* W, const std::vector<int>& qn);
+void check_err_word(unsigned* err, cudaStream_t st);
+}  // namespace pd
+
+using namespace pd;
+
+namespace {
+
+struct StepStats {
+    double energy = 0.0, trunc = 0.0, mv_ms = 0.0, mv_flops = 0.0;
+    int m = 0, matvecs = 0, nonconv = 0, steps = 0;
+    double fid_min = -1.0, fid_max = -1.0;
+    void merge(const StepStats& o) {
+        trunc = std::max(trunc, o.trunc);
+        m = std::max(m, o.m);
+        matvecs += o.matvecs;
+        nonconv += o.nonconv;
+        steps += o.steps;
+        mv_ms += o.mv_ms;
+        mv_flops += o.mv_flops;
+        if (o.fid_min >= 0) fid_min = fid_min < 0 ? o.fid_min : std::min(fid_min, o.fid_min);
+        if (o.fid_max >= 0) fid_max = std::max(fid_max, o.fid_max);
+    }
+};
+
+// One MPS segment: the whole chain (serial mode) or one region.
+struct Chain {
+    int p = 0, q = 0;                               // sites p..q
+    std::vector<Sec> bond;                          // L+1
+    std::vector<DBuf> site;                         // L, packed FP64
+    std::vector<std::unique_ptr<EnvSlab>> Lenv, Renv;   // L+1
+    std::vector<std::vector<double>> lam;           // L+1
+    int oc = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    DBuf err;
+    StepStats acc;
+    void init(int L, cudaStream_t s) {
+        bond.assign(L + 1, Sec());
+        site.clear();
+        site.resize(L);
+        Lenv.clear();
+        Renv.clear();
+        for (int i = 0; i <= L; ++i) {
+            Lenv.emplace_back(new EnvSlab());
+            Renv.emplace_back(new EnvSlab());
+        }
+        lam.assign(L + 1, {});
+        st = s;
+        err.ensure(4, st);
+        PD_CK(cudaMemsetAsync(err.p, 0, 4, st));
+    }
+    ~Chain() {
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+};
+
+}  // namespace
+
+struct dmrg_ctx {
+    int L = 0, d = 0, qtot = 0;
+    std::vector<int> qn;
+    std::vector<SiteMPO> W;
+    std::vector<std::unique_ptr<TwoSiteMPO>> w12;   // per bond (j, j+1), lazily built
+    int prec = DMRG_FP64, kmax = 8;
+    cudaStream_t base = nullptr;
+    std::unique_ptr<Chain> serial;
+    std::vector<std::unique_ptr<Chain>> reg;
+    std::vector<int> bounds;
+    std::map<int, std::vector<double>> V;   // boundary bond -> V = 1/lambda (sector order of that bond)
+    std::map<int, Sec> Vbond;
+    bool have_state = false;
+    std::string last_err;
+
+    const TwoSiteMPO& pair(int j) {
+        if (!w12[j]) w12[j].reset(new TwoSiteMPO(two_site_mpo(W[j], W[j + 1])));
+        return *w12[j];
+    }
+};
+
+namespace {
+
+const std::vector<int> kZero1 = {0};
+
+// ------------------------------------------------------------------------------------------
+// Building blocks on a chain
+// ------------------------------------------------------------------------------------------
+void make_boundary_envs(dmrg_ctx* c, Chain& ch) {
+    env_boundary(*ch.Lenv[0], ch.bond[0], c->W[0].fl, c->prec, ch.st);
+    env_boundary(*ch.Renv[c->L], ch.bond[c->L], c->W[c->L - 1].fr, c->prec, ch.st);
+}
+
+// Untruncated right-canonicalisation with the centre on site 0 (SVDs from the right).
+void right_canonicalize(dmrg_ctx* c, Chain& ch) {
+    const int L = c->L;
+    cudaStream_t st = ch.st;
+    for (int j = L - 1; j >= 1; --j) {
+        const Sec bl = ch.bond[j], br = ch.bond[j + 1];
+        long long na, nb, nl;
+        svd_split_bounds(bl, br, kZero1, c->qn, &na, &nb, &nl);
+        DBuf U, B;
+        U.ensure(std::max<long long>(1, na) * 8, st);
+        B.ensure(std::max<long long>(1, nb) * 8, st);
+        // site j viewed as a two-leg object (trivial first leg): A = U Lambda, B = V^T
+        SplitResult r = svd_split(bl, br, kZero1, c->qn, ch.site[j].as<double>(), 1 << 30, 0.0, false, 1, 0,
+                                  U.as<double>(), B.as<double>(), nullptr, st);
+        // absorb the carry U Lambda into site j-1: new[(x, s)] = old[(x, s)] carry[q]
+        const Sec& bp = ch.bond[j - 1];
+        const SiteLayout Sold = site_layout(bp, bl, c->qn);
+        const SiteLayout Snew = site_layout(bp, r.mid, c->qn);
+        const SiteLayout Sc = site_layout(bl, r.mid, kZero1);
+        GemmBatch g;
+        for (const auto& nbk : Snew.blk) {
+            int ob = Sold.at(nbk.i, nbk.s);
+            int qa = bp.q[nbk.i] + c->qn[nbk.s];
+            int ia = bl.find(qa);
+            int cb = Sc.at(ia, 0);
+            if (ob < 0 || cb < 0) continue;
+            // C(m = k, n = a_x) = sum_old carry[old][k] site[a_x][old]
+            g.add(nbk.cols, nbk.rows, nbk.off, 1, nbk.cols, bl.m[ia], 1, 1, nbk.cols,
+                  {GSeg{Sc.blk[cb].off, Sold.blk[ob].off, bl.m[ia], 0}});
+        }
+        DBuf nsite;
+        nsite.ensure(std::max<long long>(1, Snew.size) * 8, st);
+        PD_CK(cudaMemsetAsync(nsite.p, 0, std::max<long long>(1, Snew.size) * 8, st));
+        run_gemm64(g, U.as<double>(), ch.site[j - 1].as<double>(), nsite.as<double>(), st);
+        PD_CK(cudaStreamSynchronize(st));
+        ch.site[j] = std::move(B);
+        ch.site[j - 1] = std::move(nsite);
+        ch.bond[j] = r.mid;
+    }
+    const SiteLayout S0 = site_layout(ch.bond[0], ch.bond[1], c->qn);
+    double nn = dot_host(ch.site[0].as<double>(), ch.site[0].as<double>(), S0.size, st);
+    PD_REQUIRE(nn > 0 && std::isfinite(nn), DMRG_ERR_NUMERIC, "zero or non-finite initial state");
+    scale_vec(ch.site[0].as<double>(), S0.size, 1.0 / std::sqrt(nn), st);
+    ch.oc = 0;
+}
+
+void build_right_envs(dmrg_ctx* c, Chain& ch, int down_to) {
+    for (int j = c->L - 1; j >= down_to; --j) {
+        env_alloc(*ch.Renv[j], ch.bond[j], c->W[j].fl, c->prec, ch.st);
+        env_update_right(ch.bond[j], ch.bond[j + 1], c->qn, c->W[j], *ch.Renv[j + 1], ch.site[j].as<double>(),
+                         *ch.Renv[j], c->prec, ch.err.as<unsigned>(), ch.st);
+    }
+}
+
+// Davidson on psi at bond j (sites j, j+1) with the chain's environments L[j], R[j+2].
+DavResult solve_bond(dmrg_ctx* c, Chain& ch, int j, EnvSlab& Lj, EnvSlab& Rj, DBuf& psi, const dmrg_sweep_params* p,
+                     StepStats& s, double* flops_per_mv) {
+    env_make_operand(Lj, c->prec, ch.st);
+    env_make_operand(Rj, c->prec, ch.st);
+    auto plan = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), Lj.lay, Rj.lay, c->prec, ch.st);
+    DavResult r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter,
+                           ch.err.as<unsigned>(), ch.st);
+    s.matvecs += r.matvecs;
+    s.mv_ms += r.mv_ms;
+    s.mv_flops += plan->flops * r.matvecs;
+    if (r.rnorm > p->dav_tol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
+    if (flops_per_mv) *flops_per_mv = plan->flops;
+    return r;
+}
+
+// Split psi at bond j, store A/B/Lambda in the chain, update the environment behind the move.
+void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_max, bool accurate, StepStats& s,
+                    SplitResult* out = nullptr) {
+    cudaStream_t st = ch.st;
+    const Sec bl = ch.bond[j], br = ch.bond[j + 2];
+    long long na, nb, nl;
+    svd_split_bounds(bl, br, c->qn, c->qn, &na, &nb, &nl);
+    DBuf A, B;
+    A.ensure(std::max<long long>(1, na) * 8, st);
+    B.ensure(std::max<long long>(1, nb) * 8, st);
+    SplitResult r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
+                              right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st);
+    ch.bond[j + 1] = r.mid;
+    ch.lam[j + 1] = r.lam;
+    s.trunc = std::max(s.trunc, r.trunc);
+    s.m = std::max(s.m, (int)r.mid.total());
+    if (right) {
+        env_alloc(*ch.Lenv[j + 1], r.mid, c->W[j].fr, c->prec, st);
+        env_update_left(bl, r.mid, c->qn, c->W[j], *ch.Lenv[j], A.as<double>(), *ch.Lenv[j + 1], c->prec,
+                        ch.err.as<unsigned>(), st);
+        ch.oc = j + 1;
+    } else {
+        env_alloc(*ch.Renv[j + 1], r.mid, c->W[j + 1].fl, c->prec, st);
+        env_update_right(r.mid, br, c->qn, c->W[j + 1], *ch.Renv[j + 2], B.as<double>(), *ch.Renv[j + 1], c->prec,
+                         ch.err.as<unsigned>(), st);
+        ch.oc = j;
+    }
+    ch.site[j] = std::move(A);
+    ch.site[j + 1] = std::move(B);
+    if (out) *out = r;
+}
+
+void form_psi(dmrg_ctx* c, Chain& ch, int j, DBuf& psi) {
+    const PsiLayout P = psi_layout(ch.bond[j], ch.bond[j + 2], c->qn);
+    psi.ensure(std::max<long long>(1, P.size) * 8, ch.st);
+    form_two_site(ch.bond[j], ch.bond[j + 1], ch.bond[j + 2], c->qn, ch.site[j].as<double>(),
+                  ch.site[j + 1].as<double>(), nullptr, psi.as<double>(), ch.st);
+}
+
+// One two-site DMRG step at bond j (Sec. II): form Psi, Davidson, SVD + truncation, gauge move,
+// projected-operator update.
+void bond_step(dmrg_ctx* c, Chain& ch, int j, bool right, const dmrg_sweep_params* p, bool accurate = false) {
+    PD_REQUIRE(ch.oc == (right ? j : j + 1), DMRG_ERR_STATE, "orthogonality centre not at the bond");
+    DBuf psi;
+    form_psi(c, ch, j, psi);
+    StepStats& s = ch.acc;
+    DavResult r = solve_bond(c, ch, j, *ch.Lenv[j], *ch.Renv[j + 2], psi, p, s, nullptr);
+    s.energy = r.theta;
+    s.steps++;
+    split_and_move(c, ch, j, right, psi, p->m_max, accurate, s);
+}
+
+// Move the centre across bond j by an untruncated SVD (no Davidson).
+void gauge_step(dmrg_ctx* c, Chain& ch, int j, bool right) {
+    DBuf psi;
+    form_psi(c, ch, j, psi);
+    StepStats dummy;
+    split_and_move(c, ch, j, right, psi, 1 << 30, false, dummy);
+}
+
+void copy_site(DBuf& dst, const DBuf& src, long long elems, cudaStream_t st) {
+    dst.ensure(std::max<long long>(1, elems) * 8, st);
+    if (elems > 0) PD_CK(cudaMemcpyAsync(dst.p, src.p, elems * 8, cudaMemcpyDeviceToDevice, st));
+}
+
+void copy_env(EnvSlab& dst, const EnvSlab& src, cudaStream_t st) {
+    dst.lay = src.lay;
+    dst.num = src.num;
+    size_t bytes = (size_t)std::max<long long>(1, src.lay.rows) * src.lay.ld * num_size(src.num);
+    dst.buf.ensure(bytes, st);
+    PD_CK(cudaMemcpyAsync(dst.buf.p, src.buf.p, bytes, cudaMemcpyDeviceToDevice, st));
+    dst.op_valid = false;
+    dst.valid = src.valid;
+}
+
+double rayleigh_fp64(dmrg_ctx* c, Chain& ch, int j, const double* psi) {
+    // FP64 <psi|H|psi>/<psi|psi> at bond j; in mixed mode with FP64 copies of the FP32 environments
+    cudaStream_t st = ch.st;
+    EnvSlab L64, R64;
+    const EnvSlab* Lp = ch.Lenv[j].get();
+    const EnvSlab* Rp = ch.Renv[j + 2].get();
+    if (c->prec != DMRG_FP64) {
+        env_alloc(L64, ch.bond[j], c->W[j].fl, DMRG_FP64, st);
+        env_alloc(R64, ch.bond[j + 2], c->W[j + 1].fr, DMRG_FP64, st);
+        DBuf tmp;
+        tmp.ensure(std::max<long long>(1, Lp->lay.packed_size) * 8, st);
+        env_to_packed(*Lp, tmp.as<double>(), st);
+        env_from_packed(L64, tmp.as<double>(), st);
+        tmp.ensure(std::max<long long>(1, Rp->lay.packed_size) * 8, st);
+        env_to_packed(*Rp, tmp.as<double>(), st);
+        env_from_packed(R64, tmp.as<double>(), st);
+        PD_CK(cudaStreamSynchronize(st));
+        Lp = &L64;
+        Rp = &R64;
+    }
+    auto plan = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), Lp->lay, Rp->lay, DMRG_FP64, st);
+    DBuf y;
+    y.ensure(std::max<long long>(1, plan->psi.size) * 8, st);
+    heff_apply(*plan, *Lp, *Rp, psi, y.as<double>(), ch.err.as<unsigned>(), st);
+    double num = dot_host(psi, y.as<double>(), plan->psi.size, st);
+    double den = dot_host(psi, psi, plan->psi.size, st);
+    return num / den;
+}
+
+// ------------------------------------------------------------------------------------------
+// Regions
+// ------------------------------------------------------------------------------------------
+void region_half_sweep(dmrg_ctx* c, Chain& r, bool right, const dmrg_sweep_params* p) {
+    if (right) {
+        PD_REQUIRE(r.oc == r.p, DMRG_ERR_STATE, "region centre not at its left end");
+        for (int j = r.p; j < r.q; ++j) bond_step(c, r, j, true, p);
+    } else {
+        PD_REQUIRE(r.oc == r.q, DMRG_ERR_STATE, "region centre not at its right end");
+        for (int j = r.q - 1; j >= r.p; --j) bond_step(c, r, j, false, p);
+    }
+}
+
+// Run fn(i) for i in items on one host thread each (every region drives its own stream).
+template <class F>
+void parallel_items(const std::vector<int>& items, F fn) {
+    std::vector<std::thread> th;
+    std::vector<Error> errs(items.size(), Error{DMRG_OK, ""});
+    for (size_t t = 0; t < items.size(); ++t)
+        th.emplace_back([&, t]() {
+            try {
+                fn(items[t]);
+            } catch (const Error& e) {
+                errs[t] = e;
+            } catch (const std::exception& e) {
+                errs[t] = Error{DMRG_ERR_STATE, e.what()};
+            }
+        });
+    for (auto& x : th) x.join();
+    for (auto& e : errs)
+        if (e.st != DMRG_OK) throw e;
+}
+
+void stream_after(cudaStream_t waiter, cudaStream_t producer) {
+    if (waiter == producer) return;
+    cudaEvent_t ev;
+    PD_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PD_CK(cudaEventRecord(ev, producer));
+    PD_CK(cudaStreamWaitEvent(waiter, ev, 0));
+    PD_CK(cudaEventDestroy(ev));
+}
+
+// Merge at boundary k between regions k-1 and k: Psi' = psi'_3 V psi'_4 (Eq. merge), Davidson on
+// the shared bond with the left region's L and the right region's R environment, accurate SVD,
+// new split psi_3 = A Lambda, psi_4 = Lambda B, V = 1/Lambda (Eqs. inverse, isvd), and the
+// environment hand-off.
+void do_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fid_out, double* e_out) {
+    Chain& left = *c->reg[k - 1];
+    Chain& right = *c->reg[k];
+    const int b = c->bounds[k];
+    PD_REQUIRE(left.oc == b - 1 && right.oc == b, DMRG_ERR_STATE, "regions are not both at the shared bond");
+    cudaStream_t st = left.st;
+    stream_after(st, right.st);
+    const Sec bm = c->Vbond.at(b);
+    PD_REQUIRE(left.bond[b] == bm && right.bond[b] == bm, DMRG_ERR_STATE, "boundary bond changed since the split");
+    const Sec bl = left.bond[b - 1], br = right.bond[b + 1];
+    DBuf Vd;
+    upload(Vd, c->V.at(b), st);
+    const PsiLayout P = psi_layout(bl, br, c->qn);
+    DBuf psi;
+    psi.ensure(std::max<long long>(1, P.size) * 8, st);
+    form_two_site(bl, bm, br, c->qn, left.site[b - 1].as<double>(), right.site[b].as<double>(), Vd.as<double>(),
+                  psi.as<double>(), st);
+    double nn = dot_host(psi.as<double>(), psi.as<double>(), P.size, st);
+    PD_REQUIRE(nn > 0 && std::isfinite(nn), DMRG_ERR_NUMERIC, "merged wavefunction is zero or non-finite");
+    scale_vec(psi.as<double>(), P.size, 1.0 / std::sqrt(nn), st);
+    DBuf guess;
+    copy_site(guess, psi, P.size, st);
+    EnvSlab& Lj = *left.Lenv[b - 1];
+    EnvSlab& Rj = *right.Renv[b + 1];
+    env_make_operand(Lj, c->prec, st);
+    env_make_operand(Rj, c->prec, st);
+    auto plan = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, c->prec, st);
+    DavResult r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter,
+                           left.err.as<unsigned>(), st);
+    StepStats& s = left.acc;
+    s.matvecs += r.matvecs;
+    s.mv_ms += r.mv_ms;
+    s.mv_flops += plan->flops * r.matvecs;
+    if (r.rnorm > p->dav_tol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
+    double ov = dot_host(guess.as<double>(), psi.as<double>(), P.size, st);
+    double fid = 1.0 - std::fabs(ov);
+    s.energy = r.theta;
+    s.steps++;
+    s.fid_min = s.fid_min < 0 ? fid : std::min(s.fid_min, fid);
+    s.fid_max = std::max(s.fid_max, fid);
+    long long na, nb, nl;
+    svd_split_bounds(bl, br, c->qn, c->qn, &na, &nb, &nl);
+    DBuf A, B;
+    A.ensure(std::max<long long>(1, na) * 8, st);
+    B.ensure(std::max<long long>(1, nb) * 8, st);
+    SplitResult sr = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), p->m_max, 1e-12, true, 0, 0, A.as<double>(),
+                               B.as<double>(), nullptr, st);
+    s.trunc = std::max(s.trunc, sr.trunc);
+    s.m = std::max(s.m, (int)sr.mid.total());
+    DBuf lamd;
+    upload(lamd, sr.lam, st);
+    // new projected operators for both sides (Sec. II: each side's operators in its own basis)
+    std::unique_ptr<EnvSlab> Lnew(new EnvSlab()), Rnew(new EnvSlab());
+    env_alloc(*Lnew, sr.mid, c->W[b - 1].fr, c->prec, st);
+    env_update_left(bl, sr.mid, c->qn, c->W[b - 1], Lj, A.as<double>(), *Lnew, c->prec, left.err.as<unsigned>(), st);
+    env_alloc(*Rnew, sr.mid, c->W[b].fl, c->prec, st);
+    env_update_right(sr.mid, br, c->qn, c->W[b], Rj, B.as<double>(), *Rnew, c->prec, left.err.as<unsigned>(), st);
+    // psi_3 = A Lambda for the left region, psi_4 = Lambda B for the right region
+    const SiteLayout SA = site_layout(bl, sr.mid, c->qn), SB = site_layout(sr.mid, br, c->qn);
+    DBuf psi3, psi4;
+    psi3.ensure(std::max<long long>(1, SA.size) * 8, st);
+    psi4.ensure(std::max<long long>(1, SB.size) * 8, st);
+    scale_site(bl, sr.mid, c->qn, A.as<double>(), lamd.as<double>(), true, psi3.as<double>(), st);
+    scale_site(sr.mid, br, c->qn, B.as<double>(), lamd.as<double>(), false, psi4.as<double>(), st);
+    check_err_word(left.err.as<unsigned>(), st);
+    std::vector<double> V(sr.lam.size());
+    for (size_t i = 0; i < V.size(); ++i) V[i] = 1.0 / sr.lam[i];
+    c->V[b] = V;
+    c->Vbond[b] = sr.mid;
+    left.bond[b] = sr.mid;
+    right.bond[b] = sr.mid;
+    left.lam[b] = sr.lam;
+    right.lam[b] = sr.lam;
+    left.site[b - 1] = std::move(psi3);
+    right.site[b] = std::move(psi4);
+    left.Renv[b] = std::move(Rnew);
+    right.Lenv[b] = std::move(Lnew);
+    PD_CK(cudaStreamSynchronize(st));
+    stream_after(right.st, st);
+    if (fid_out) *fid_out = fid;
+    if (e_out) *e_out = r.theta;
+}
+
+// Serial set-up of the regions (warm-up, split at every boundary while sweeping left,
+// staggered positions).
+void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
+    Chain& ch = *c->serial;
+    const int L = c->L;
+    PD_REQUIRE(ch.oc == 0, DMRG_ERR_STATE, "set-up needs the serial centre on site 0");
+    std::vector<int> bounds(R + 1);
+    for (int k = 0; k <= R; ++k) bounds[k] = (int)std::lround((double)k * L / R);
+    for (int k = 0; k < R; ++k)
+        PD_REQUIRE(bounds[k + 1] - bounds[k] >= 2, DMRG_ERR_ARG, "every region needs at least two sites");
+    for (int j = 0; j + 1 < L; ++j) c->pair(j);   // build shared read-only data before threads start
+    for (int w = 0; w + 1 < warmup; ++w) {
+        for (int j = 0; j <= L - 2; ++j) bond_step(c, ch, j, true, p);
+        for (int j = L - 2; j >= 0; --j) bond_step(c, ch, j, false, p);
+    }
+    for (int j = 0; j <= L - 2; ++j) {
+        if (warmup > 0) bond_step(c, ch, j, true, p);
+        else gauge_step(c, ch, j, true);
+    }
+    std::map<int, int> bidx;
+    for (int k = 1; k < R; ++k) bidx[bounds[k]] = k;
+    std::vector<DBuf> left_end(R);
+    std::vector<std::unique_ptr<EnvSlab>> left_env(R);
+    cudaStream_t st = ch.st;
+    for (int j = L - 2; j >= 0; --j) {
+        const int b = j + 1;
+        const bool split = bidx.count(b) > 0;
+        if (!split) {
+            if (warmup > 0) bond_step(c, ch, j, false, p);
+            else gauge_step(c, ch, j, false);
+            continue;
+        }
+        DBuf psi;
+        form_psi(c, ch, j, psi);
+        StepStats& s = ch.acc;
+        int m_max = warmup > 0 ? p->m_max : (1 << 30);
+        if (warmup > 0) {
+            DavResult r = solve_bond(c, ch, j, *ch.Lenv[j], *ch.Renv[j + 2], psi, p, s, nullptr);
+            s.energy = r.theta;
+            s.steps++;
+        }
+        const Sec bl = ch.bond[j], br = ch.bond[j + 2];
+        long long na, nb, nl;
+        svd_split_bounds(bl, br, c->qn, c->qn, &na, &nb, &nl);
+        DBuf A, B;
+        A.ensure(std::max<long long>(1, na) * 8, st);
+        B.ensure(std::max<long long>(1, nb) * 8, st);
+        SplitResult sr = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, warmup > 0, 0, 0,
+                                   A.as<double>(), B.as<double>(), nullptr, st);
+        DBuf lamd;
+        upload(lamd, sr.lam, st);
+        const int k = bidx[b];
+        // region k: left-end centre Lambda B and its left environment built from A
+        const SiteLayout SA = site_layout(bl, sr.mid, c->qn), SB = site_layout(sr.mid, br, c->qn);
+        left_end[k].ensure(std::max<long long>(1, SB.size) * 8, st);
+        scale_site(sr.mid, br, c->qn, B.as<double>(), lamd.as<double>(), false, left_end[k].as<double>(), st);
+        left_env[k].reset(new EnvSlab());
+        env_alloc(*left_env[k], sr.mid, c->W[j].fr, c->prec, st);
+        env_update_left(bl, sr.mid, c->qn, c->W[j], *ch.Lenv[j], A.as<double>(), *left_env[k], c->prec,
+                        ch.err.as<unsigned>(), st);
+        // serial chain continues left with A Lambda
+        DBuf AL;
+        AL.ensure(std::max<long long>(1, SA.size) * 8, st);
+        scale_site(bl, sr.mid, c->qn, A.as<double>(), lamd.as<double>(), true, AL.as<double>(), st);
+        ch.bond[b] = sr.mid;
+        ch.lam[b] = sr.lam;
+        env_alloc(*ch.Renv[b], sr.mid, c->W[j + 1].fl, c->prec, st);
+        env_update_right(sr.mid, br, c->qn, c->W[j + 1], *ch.Renv[j + 2], B.as<double>(), *ch.Renv[b], c->prec,
+                         ch.err.as<unsigned>(), st);
+        ch.site[j] = std::move(AL);
+        ch.site[j + 1] = std::move(B);
+        ch.oc = j;
+        std::vector<double> V(sr.lam.size());
+        for (size_t i = 0; i < V.size(); ++i) V[i] = 1.0 / sr.lam[i];
+        c->V[b] = V;
+        c->Vbond[b] = sr.mid;
+    }
+    check_err_word(ch.err.as<unsigned>(), st);
+    PD_CK(cudaStreamSynchronize(st));
+    // hand the tensors to the regions
+    c->bounds = bounds;
+    c->reg.clear();
+    for (int k = 0; k < R; ++k) {
+        std::unique_ptr<Chain> r(new Chain());
+        cudaStream_t rs;
+        PD_CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+        r->init(L, rs);
+        r->own_stream = true;
+        r->p = bounds[k];
+        r->q = bounds[k + 1] - 1;
+        for (int b = r->p; b <= r->q + 1; ++b) {
+            r->bond[b] = ch.bond[b];
+            r->lam[b] = ch.lam[b];
+        }
+        for (int sidx = r->p; sidx <= r->q; ++sidx) r->site[sidx] = std::move(ch.site[sidx]);
+        if (k > 0) {
+            r->site[r->p] = std::move(left_end[k]);
+            r->Lenv[r->p] = std::move(left_env[k]);
+        } else {
+            r->Lenv[0] = std::move(ch.Lenv[0]);
+        }
+        for (int b = r->p + 1; b <= r->q + 1; ++b) r->Renv[b] = std::move(ch.Renv[b]);
+        r->oc = r->p;
+        c->reg.push_back(std::move(r));
+    }
+    // staggered start (Fig. 4): even regions (1-based) move to their right end
+    std::vector<int> odd;
+    for (int k = 1; k < R; k += 2) odd.push_back(k);
+    parallel_items(odd, [&](int k) {
+        region_half_sweep(c, *c->reg[k], true, p);
+        check_err_word(c->reg[k]->err.as<unsigned>(), c->reg[k]->st);
+    });
+}
+
+// One parallel sweep, Fig. 4 (a)-(d).
+StepStats region_sweep(dmrg_ctx* c, const dmrg_sweep_params* p) {
+    const int R = (int)c->reg.size();
+    for (auto& r : c->reg) r->acc = StepStats();
+    std::vector<int> all(R), mb, md;
+    for (int k = 0; k < R; ++k) all[k] = k;
+    for (int k = 1; k < R; k += 2) mb.push_back(k);
+    for (int k = 2; k < R; k += 2) md.push_back(k);
+    double e_last = 0.0;
+    auto half = [&](bool first) {
+        parallel_items(all, [&](int k) {
+            bool right = (k % 2 == 0) == first;
+            region_half_sweep(c, *c->reg[k], right, p);
+            check_err_word(c->reg[k]->err.as<unsigned>(), c->reg[k]->st);
+        });
+    };
+    std::vector<double> e_merge(R, 0.0);
+    half(true);                                                         // (a)
+    parallel_items(mb, [&](int k) { do_merge(c, k, p, nullptr, &e_merge[k]); });   // (b)
+    if (!mb.empty()) e_last = e_merge[mb.back()];
+    half(false);                                                        // (c)
+    parallel_items(md, [&](int k) { do_merge(c, k, p, nullptr, &e_merge[k]); });   // (d)
+    if (!md.empty()) e_last = e_merge[md.back()];
+    StepStats tot;
+    for (auto& r : c->reg) tot.merge(r->acc);
+    tot.energy = e_last;
+    return tot;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+#define CTX_TRY try {
+#define CTX_CATCH(ctx)                                        \
+    }                                                         \
+    catch (const Error& e) {                                  \
+        if (ctx) (ctx)->last_err = e.msg;                     \
+        g_last_error = e.msg;                                 \
+        return e.st;                                          \
+    }                                                         \
+    catch (const std::exception& e) {                         \
+        if (ctx) (ctx)->last_err = e.what();                  \
+        g_last_error = e.what();                              \
+        return DMRG_ERR_STATE;                                \
+    }
+
+extern "C" {
+
+dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_config* cfg) {
+    dmrg_ctx* c = nullptr;
+    CTX_TRY
+    PD_REQUIRE(out && mpo && cfg, DMRG_ERR_ARG, "null argument");
+    *out = nullptr;
+    PD_REQUIRE(mpo->n_sites >= 2 && mpo->d >= 1 && mpo->d <= 8, DMRG_ERR_ARG, "bad n_sites or d");
+    PD_REQUIRE(mpo->qn_local && mpo->D && mpo->flux && mpo->W, DMRG_ERR_ARG, "null MPO array");
+    PD_REQUIRE(cfg->precision == DMRG_FP64 || cfg->precision == DMRG_TF32 || cfg->precision == DMRG_BF16,
+               DMRG_ERR_ARG, "unknown precision");
+    PD_REQUIRE(cfg->precision == DMRG_FP64 || tc_available(), DMRG_ERR_STATE, "tensor-core engine unavailable");
+    std::unique_ptr<dmrg_ctx> C(new dmrg_ctx());
+    c = C.get();
+    C->L = mpo->n_sites;
+    C->d = mpo->d;
+    C->qtot = mpo->qn_total;
+    C->qn.assign(mpo->qn_local, mpo->qn_local + mpo->d);
+    C->prec = cfg->precision;
+    C->kmax = cfg->kmax > 0 ? cfg->kmax : 8;
+    PD_REQUIRE(C->kmax >= 2 && C->kmax <= 32, DMRG_ERR_ARG, "kmax must be in [2, 32]");
+    C->base = (cudaStream_t)cfg->stream;
+    PD_REQUIRE(mpo->D[0] == 1 && mpo->D[C->L] == 1, DMRG_ERR_ARG, "D[0] and D[L] must be 1");
+    size_t woff = 0, foff = 0;
+    for (int j = 0; j < C->L; ++j) {
+        int Dl = mpo->D[j], Dr = mpo->D[j + 1];
+        PD_REQUIRE(Dl > 0 && Dr > 0, DMRG_ERR_ARG, "MPO bond dimension must be positive");
+        C->W.push_back(make_site_mpo(Dl, Dr, C->d, mpo->flux + foff, mpo->flux + foff + Dl, mpo->W + woff, C->qn));
+        woff += (size_t)Dl * C->d * C->d * Dr;
+        foff += Dl;
+    }
+    C->w12.resize(C->L);
+    *out = C.release();
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_set_mps(dmrg_ctx* c, const dmrg_mps_desc* m) {
+    CTX_TRY
+    PD_REQUIRE(c && m && m->n_sectors && m->sector_q && m->sector_m && m->data, DMRG_ERR_ARG, "null argument");
+    c->reg.clear();
+    c->bounds.clear();
+    c->V.clear();
+    c->Vbond.clear();
+    c->serial.reset(new Chain());
+    Chain& ch = *c->serial;
+    ch.init(c->L, c->base);
+    ch.p = 0;
+    ch.q = c->L - 1;
+    size_t so = 0;
+    for (int b = 0; b <= c->L; ++b) {
+        ch.bond[b] = make_sec(m->n_sectors[b], m->sector_q + so, m->sector_m + so);
+        so += m->n_sectors[b];
+    }
+    PD_REQUIRE(ch.bond[0].n() == 1 && ch.bond[0].q[0] == 0 && ch.bond[0].m[0] == 1, DMRG_ERR_QN,
+               "bond 0 must be the single sector {0: 1}");
+    PD_REQUIRE(ch.bond[c->L].n() == 1 && ch.bond[c->L].q[0] == c->qtot && ch.bond[c->L].m[0] == 1, DMRG_ERR_QN,
+               "bond L must be the single sector {qn_total: 1}");
+    size_t off = 0;
+    for (int j = 0; j < c->L; ++j) {
+        const SiteLayout S = site_layout(ch.bond[j], ch.bond[j + 1], c->qn);
+        ch.site[j].ensure(std::max<long long>(1, S.size) * 8, ch.st);
+        if (S.size) PD_CK(cudaMemcpyAsync(ch.site[j].p, m->data + off, S.size * 8, cudaMemcpyHostToDevice, ch.st));
+        off += S.size;
+    }
+    PD_CK(cudaStreamSynchronize(ch.st));
+    right_canonicalize(c, ch);
+    make_boundary_envs(c, ch);
+    build_right_envs(c, ch, 2);
+    check_err_word(ch.err.as<unsigned>(), ch.st);
+    c->have_state = true;
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_sweep(dmrg_ctx* c, const dmrg_sweep_params* p, dmrg_sweep_stats* stats) {
+    CTX_TRY
+    PD_REQUIRE(c && p, DMRG_ERR_ARG, "null argument");
+    PD_REQUIRE(c->have_state, DMRG_ERR_STATE, "no state loaded");
+    PD_REQUIRE(p->m_max >= 1 && p->dav_max_iter >= 1 && p->dav_tol >= 0, DMRG_ERR_ARG, "bad sweep parameters");
+    auto t0 = std::chrono::steady_clock::now();
+    StepStats tot;
+    if (c->reg.empty()) {
+        Chain& ch = *c->serial;
+        ch.acc = StepStats();
+        PD_REQUIRE(ch.oc == 0, DMRG_ERR_STATE, "serial sweep must start with the centre on site 0");
+        for (int j = 0; j <= c->L - 2; ++j) bond_step(c, ch, j, true, p);
+        for (int j = c->L - 2; j >= 0; --j) bond_step(c, ch, j, false, p);
+        check_err_word(ch.err.as<unsigned>(), ch.st);
+        tot = ch.acc;
+        tot.energy = ch.acc.energy;
+    } else {
+        tot = region_sweep(c, p);
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    if (stats) {
+        stats->energy = tot.energy;
+        stats->max_trunc_err = tot.trunc;
+        stats->max_m = tot.m;
+        stats->n_matvec = tot.matvecs;
+        stats->n_steps = tot.steps;
+        stats->dav_nonconv = tot.nonconv;
+        stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+        stats->matvec_seconds = tot.mv_ms * 1e-3;
+        stats->matvec_flops = tot.mv_flops;
+        stats->min_fidelity = tot.fid_min;
+        stats->max_fidelity = tot.fid_max;
+    }
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_setup_regions(dmrg_ctx* c, int n_regions, int warmup, const dmrg_sweep_params* p) {
+    CTX_TRY
+    PD_REQUIRE(c && p, DMRG_ERR_ARG, "null argument");
+    PD_REQUIRE(c->have_state, DMRG_ERR_STATE, "no state loaded");
+    PD_REQUIRE(n_regions >= 1 && warmup >= 0, DMRG_ERR_ARG, "bad region count or warm-up");
+    PD_REQUIRE(c->reg.empty(), DMRG_ERR_STATE, "regions are already set up");
+    if (n_regions == 1) return DMRG_OK;
+    setup_regions(c, n_regions, warmup, p);
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fidelity_out, double* energy_out) {
+    CTX_TRY
+    PD_REQUIRE(c && p, DMRG_ERR_ARG, "null argument");
+    PD_REQUIRE(!c->reg.empty() && k >= 1 && k < (int)c->reg.size(), DMRG_ERR_ARG, "no such boundary");
+    do_merge(c, k, p, fidelity_out, energy_out);
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_energy(dmrg_ctx* c, double* E) {
+    CTX_TRY
+    PD_REQUIRE(c && E, DMRG_ERR_ARG, "null argument");
+    PD_REQUIRE(c->have_state && c->reg.empty(), DMRG_ERR_STATE, "energy needs a serial state");
+    Chain& ch = *c->serial;
+    int j = std::min(ch.oc, c->L - 2);
+    DBuf psi;
+    form_psi(c, ch, j, psi);
+    *E = rayleigh_fp64(c, ch, j, psi.as<double>());
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_get_bond(dmrg_ctx* c, int b, int* q, int* m, int cap, int* n) {
+    CTX_TRY
+    PD_REQUIRE(c && n && c->have_state && b >= 0 && b <= c->L, DMRG_ERR_ARG, "bad argument");
+    const Chain* ch = c->serial.get();
+    if (!c->reg.empty())
+        for (const auto& r : c->reg)
+            if (b >= r->p && b <= r->q + 1) { ch = r.get(); break; }
+    const Sec& s = ch->bond[b];
+    *n = s.n();
+    PD_REQUIRE(s.n() <= cap && q && m, DMRG_ERR_CAPACITY, "capacity too small");
+    for (int i = 0; i < s.n(); ++i) { q[i] = s.q[i]; m[i] = s.m[i]; }
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_get_lambda(dmrg_ctx* c, int b, double* lam, int cap, int* n) {
+    CTX_TRY
+    PD_REQUIRE(c && n && c->have_state && b >= 0 && b <= c->L, DMRG_ERR_ARG, "bad argument");
+    const Chain* ch = c->serial.get();
+    if (!c->reg.empty())
+        for (const auto& r : c->reg)
+            if (b >= r->p && b <= r->q + 1) { ch = r.get(); break; }
+    const auto& v = ch->lam[b];
+    *n = (int)v.size();
+    PD_REQUIRE((int)v.size() <= cap && lam, DMRG_ERR_CAPACITY, "capacity too small");
+    for (size_t i = 0; i < v.size(); ++i) lam[i] = v[i];
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_get_center(dmrg_ctx* c, int region, int* site) {
+    CTX_TRY
+    PD_REQUIRE(c && site && c->have_state, DMRG_ERR_ARG, "bad argument");
+    if (c->reg.empty()) *site = c->serial->oc;
+    else {
+        PD_REQUIRE(region >= 0 && region < (int)c->reg.size(), DMRG_ERR_ARG, "no such region");
+        *site = c->reg[region]->oc;
+    }
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_destroy(dmrg_ctx* c) {
+    if (!c) return DMRG_OK;
+    cudaStream_t st = c->base;
+    cudaStreamSynchronize(st);
+    for (auto& r : c->reg)
+        if (r->st) cudaStreamSynchronize(r->st);
+    delete c;
+    return DMRG_OK;
+}
+
+const char* dmrg_last_error(const dmrg_ctx* c) {
+    if (c) return c->last_err.c_str();
+    return g_last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations of the pdmrg engine (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pdmrg.h"
+
+namespace pd {
+
+// ------------------------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------------------------
+struct Error {
+    dmrg_status st;
+    std::string msg;
+};
+
+#define PD_CK(x)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (x);                                                             \
+        if (e_ != cudaSuccess)                                                            \
+            throw ::pd::Error{e_ == cudaErrorMemoryAllocation ? DMRG_ERR_OOM : DMRG_ERR_CUDA, \
+                              std::string(#x) + ": " + cudaGetErrorString(e_)};            \
+    } while (0)
+
+#define PD_REQUIRE(cond, code, what)                                                      \
+    do {                                                                                  \
+        if (!(cond)) throw ::pd::Error{code, what};                                       \
+    } while (0)
+
+// Device error word bits (written by kernels, read by the host after a step).
+enum : unsigned {
+    ERRBIT_TIMEOUT = 1u,      // a bounded mbarrier wait ran out
+    ERRBIT_NONFINITE = 2u,    // NaN/Inf seen in a checked vector
+    ERRBIT_BOUNDS = 4u,       // an index check failed (access skipped)
+};
+
+// ------------------------------------------------------------------------------------------
+// Grouped GEMM contract shared by the FP64 SIMT engine and the tcgen05 engine:
+//   C(m, n) (+)= alpha * sum_segments sum_k A(m, k) B(n, k)
+//   A(m, k) = A[a_off + m*sam + k*sak], B(n, k) = B[b_off + n*sbn + k*sbk],
+//   C(m, n) = C[c_off + m*scm + n*scn].
+// The tensor-core engine requires sak = sbk = scm = 1, a uniform sam (= lda) per launch for A
+// and sbn (= ldb) for B, and zero padding of every operand row up to the K tile.
+// ------------------------------------------------------------------------------------------
+struct GSeg {
+    long long a_off, b_off;
+    int K;
+    int pad_;
+};
+struct GProb {
+    int M, N;
+    int seg0, nseg;
+    long long c_off;
+    int sam, sak, sbn, sbk, scm, scn;
+    int accumulate;       // 0: C = alpha*AB, 1: C += alpha*AB
+    int pad_;
+    double alpha;
+};
+struct GTile {
+    int prob, m0, n0, pad_;
+};
+
+// Block copy job: dst[r*drs + c*dcs] = scale * src[r*srs + c*scs] for r < rows, c < cols;
+// zero columns cols <= c < zero_to (row-major destination only, dcs = 1).
+struct CopyJob {
+    long long src, dst;
+    int rows, cols;
+    int srs, scs, drs, dcs;
+    int zero_to;
+    int pad_;
+    double scale;
+};
+
+// Linear combination of blocks: out[r*ldo + c] = sum_t coef_t * in[src_t + r*ld_t + c],
+// zero-filled for cols <= c < zero_to.
+struct MixJob {
+    long long dst;
+    int rows, cols, ldo, zero_to;
+    int t0, nt;
+};
+struct MixTerm {
+    long long src;
+    int ld, pad_;
+    double coef;
+};
+
+// Diagonal of H_eff: out[off + a*cols + c] = sum_t coef_t * Ld_t[a] * Rd_t[c], where
+// Ld_t[a] = Lslab[l_t + a*(ldl+1)], Rd_t[c] = Rslab[r_t + c*(ldr+1)].
+struct DiagJob {
+    long long off;
+    int rows, cols, t0, nt;
+};
+struct DiagTerm {
+    long long l, r;
+    double coef;
+};
+
+// ------------------------------------------------------------------------------------------
+// Launch wrappers (kernels.cu)
+// ------------------------------------------------------------------------------------------
+void launch_gemm64(const GProb* probs, const GSeg* segs, const GTile* tiles, int ntiles,
+                   const double* A, const double* B, double* C, cudaStream_t st);
+
+template <class Tin, class Tout>
+void launch_copy(const CopyJob* jobs, int njobs, int max_elems, const Tin* src, Tout* dst,
+                 cudaStream_t st);
+
+template <class Tin, class Tout>
+void launch_mix(const MixJob* jobs, int njobs, int max_elems, const MixTerm* terms,
+                const Tin* in, Tout* out, cudaStream_t st);
+
+template <class T>
+void launch_diag(const DiagJob* jobs, int njobs, int max_elems, const DiagTerm* terms,
+                 const T* Lslab, int ldl, const T* Rslab, int ldr, double* out, cudaStream_t st);
+
+// Davidson helpers (all FP64, vectors of length n, basis rows of stride ldv)
+void launch_dots(const double* V, long long ldv, int k, const double* y, long long n,
+                 double* partial, int nchunks, double* out, cudaStream_t st);
+void launch_ritz(const double* V, const double* AV, long long ldv, int k, const double* yth,
+                 long long n, double* u, double* Au, double* r, double* partial, int nchunks,
+                 double* norms, cudaStream_t st);
+void launch_precond(const double* r, const double* diag, const double* theta, double floor_,
+                    long long n, double* t, cudaStream_t st);
+void launch_subtract(const double* V, long long ldv, int k, const double* c, long long n,
+                     double* t, cudaStream_t st);
+void launch_scale(const double* x, const double* nrm2, long long n, double* y, int invert_sqrt,
+                  cudaStream_t st);
+void launch_small_eig(const double* G, int k, int ldg, double* yth, cudaStream_t st);
+void launch_nrm2(const double* x, long long n, double* partial, int nchunks, double* out,
+                 cudaStream_t st);
+void launch_finite_check(const double* x, long long n, unsigned* err, cudaStream_t st);
+
+// One-sided Jacobi SVD over a batch of column-major matrices W_s (p_s x n_s, n_s <= p_s)
+struct SvdSec {
+    long long w_off;      // W: p x n column-major
+    long long v_off;      // V: n x n column-major
+    long long s_off;      // singular values / order buffers (n entries)
+    int p, n;
+    int npad;             // n rounded up to even
+    int pair0;            // first global pair index of this sector in a round
+};
+void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, double* V, cudaStream_t st);
+void launch_jacobi_round(const SvdSec* secs, const int* pair_sec, int npairs, int round,
+                         double* W, double* V, double tol, int* rotated, cudaStream_t st);
+void launch_svd_finish(const SvdSec* secs, int nsec, int max_n, const double* W, double* sig,
+                       int* order, cudaStream_t st);
+
+// Truncation selection over all sectors (single CTA).  sig sorted per sector by `order`.
+void launch_truncate(const SvdSec* secs, int nsec, const double* sig, const int* order,
+                     int total, int m_max, double rel_cutoff, double degen_tol, int* kept,
+                     double* weights, cudaStream_t st);
+
+}  // namespace pd

@@ -1,0 +1,1118 @@
+// Contraction plans and device building blocks of the two-site DMRG step (Sec. II).
+#include <cfloat>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+#include "plans.h"
+
+namespace pd {
+
+// ------------------------------------------------------------------------------------------
+// Layouts
+// ------------------------------------------------------------------------------------------
+SiteLayout site_layout(const Sec& bl, const Sec& br, const std::vector<int>& qn) {
+    SiteLayout L;
+    L.d = (int)qn.size();
+    L.index.assign((size_t)bl.n() * L.d, -1);
+    long long off = 0;
+    for (int i = 0; i < bl.n(); ++i)
+        for (int s = 0; s < L.d; ++s) {
+            int j = br.find(bl.q[i] + qn[s]);
+            if (j < 0) continue;
+            L.index[(size_t)i * L.d + s] = (int)L.blk.size();
+            L.blk.push_back({i, s, j, off, bl.m[i], br.m[j]});
+            off += (long long)bl.m[i] * br.m[j];
+        }
+    L.size = off;
+    return L;
+}
+
+PsiLayout psi_layout2(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2) {
+    PsiLayout P;
+    P.d1 = (int)qn1.size();
+    P.d2 = (int)qn2.size();
+    P.d = P.d1;
+    P.index.assign((size_t)bl.n() * P.d1 * P.d2, -1);
+    long long off = 0;
+    for (int i = 0; i < bl.n(); ++i)
+        for (int s1 = 0; s1 < P.d1; ++s1)
+            for (int s2 = 0; s2 < P.d2; ++s2) {
+                int k = br.find(bl.q[i] + qn1[s1] + qn2[s2]);
+                if (k < 0) continue;
+                P.index[((size_t)i * P.d1 + s1) * P.d2 + s2] = (int)P.blk.size();
+                P.blk.push_back({i, s1, s2, k, off, bl.m[i], br.m[k]});
+                off += (long long)bl.m[i] * br.m[k];
+            }
+    P.size = off;
+    return P;
+}
+
+PsiLayout psi_layout(const Sec& bl, const Sec& br, const std::vector<int>& qn) { return psi_layout2(bl, br, qn, qn); }
+
+EnvLayout env_layout(const Sec& b, const std::vector<int>& flux, int ld) {
+    EnvLayout E;
+    E.D = (int)flux.size();
+    E.ld = ld;
+    E.index.assign((size_t)b.n() * E.D, -1);
+    long long row = 0, packed = 0;
+    for (int i = 0; i < b.n(); ++i)
+        for (int w = 0; w < E.D; ++w) {
+            int k = b.find(b.q[i] - flux[w]);
+            if (k < 0) continue;
+            E.index[(size_t)i * E.D + w] = (int)E.blk.size();
+            E.blk.push_back({i, w, k, row, packed, b.m[i], b.m[k]});
+            row += b.m[i];
+            packed += (long long)b.m[i] * b.m[k];
+        }
+    E.rows = row;
+    E.packed_size = packed;
+    return E;
+}
+
+TwoSiteMPO two_site_mpo(const SiteMPO& a, const SiteMPO& b) {
+    TwoSiteMPO T;
+    const int d = a.d;
+    T.D0 = a.Dl;
+    T.D2 = b.Dr;
+    T.d = d;
+    T.f0 = a.fl;
+    T.f2 = b.fr;
+    std::vector<double> acc((size_t)a.Dl * d * d * d * d * b.Dr, 0.0);
+    auto idx = [&](int w, int s1, int s1p, int s2, int s2p, int w2) {
+        return (((((size_t)w * d + s1) * d + s1p) * d + s2) * d + s2p) * b.Dr + w2;
+    };
+    for (int w = 0; w < a.Dl; ++w)
+        for (int s1 = 0; s1 < d; ++s1)
+            for (int s1p = 0; s1p < d; ++s1p)
+                for (int w1 = 0; w1 < a.Dr; ++w1) {
+                    double x = a.at(w, s1, s1p, w1);
+                    if (x == 0.0) continue;
+                    for (int s2 = 0; s2 < d; ++s2)
+                        for (int s2p = 0; s2p < d; ++s2p)
+                            for (int w2 = 0; w2 < b.Dr; ++w2) {
+                                double y = b.at(w1, s2, s2p, w2);
+                                if (y != 0.0) acc[idx(w, s1, s1p, s2, s2p, w2)] += x * y;
+                            }
+                }
+    for (int w = 0; w < a.Dl; ++w)
+        for (int s1 = 0; s1 < d; ++s1)
+            for (int s1p = 0; s1p < d; ++s1p)
+                for (int s2 = 0; s2 < d; ++s2)
+                    for (int s2p = 0; s2p < d; ++s2p)
+                        for (int w2 = 0; w2 < b.Dr; ++w2) {
+                            double v = acc[idx(w, s1, s1p, s2, s2p, w2)];
+                            if (v != 0.0) T.nz.push_back({w, s1, s1p, s2, s2p, w2, v});
+                        }
+    return T;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batches and job lists
+// ------------------------------------------------------------------------------------------
+void GemmBatch::upload_tiles(int tm, int tn, cudaStream_t st) {
+    if (tile_m == tm && tile_n == tn && dtiles.p) return;
+    std::vector<GTile> tiles;
+    for (int p = 0; p < (int)probs.size(); ++p)
+        for (int m0 = 0; m0 < probs[p].M; m0 += tm)
+            for (int n0 = 0; n0 < probs[p].N; n0 += tn) tiles.push_back({p, m0, n0, 0});
+    ntiles = (int)tiles.size();
+    upload(dprobs, probs, st);
+    upload(dsegs, segs, st);
+    upload(dtiles, tiles, st);
+    tile_m = tm;
+    tile_n = tn;
+}
+
+void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st) {
+    if (g.empty()) return;
+    g.upload_tiles(64, 64, st);
+    launch_gemm64(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);
+}
+
+template <class Tin>
+void run_copy(const CopyList& c, const Tin* src, void* dst, Num out, cudaStream_t st) {
+    if (c.jobs.empty()) return;
+    const CopyJob* j = c.d.as<CopyJob>();
+    int n = (int)c.jobs.size();
+    if (out == Num::F64) launch_copy<Tin, double>(j, n, c.max_elems, src, (double*)dst, st);
+    else if (out == Num::F32) launch_copy<Tin, float>(j, n, c.max_elems, src, (float*)dst, st);
+    else launch_copy<Tin, __nv_bfloat16>(j, n, c.max_elems, src, (__nv_bfloat16*)dst, st);
+}
+template void run_copy<double>(const CopyList&, const double*, void*, Num, cudaStream_t);
+template void run_copy<float>(const CopyList&, const float*, void*, Num, cudaStream_t);
+
+template <>
+void run_mix<double>(const MixList& m, const double* in, void* out, Num t, cudaStream_t st) {
+    if (m.jobs.empty()) return;
+    PD_REQUIRE(t == Num::F64, DMRG_ERR_ARG, "FP64 mix output must be FP64");
+    launch_mix<double, double>(m.dj.as<MixJob>(), (int)m.jobs.size(), m.max_elems, m.dt.as<MixTerm>(), in, (double*)out, st);
+}
+template <>
+void run_mix<float>(const MixList& m, const float* in, void* out, Num t, cudaStream_t st) {
+    if (m.jobs.empty()) return;
+    if (t == Num::F32)
+        launch_mix<float, float>(m.dj.as<MixJob>(), (int)m.jobs.size(), m.max_elems, m.dt.as<MixTerm>(), in, (float*)out, st);
+    else
+        launch_mix<float, __nv_bfloat16>(m.dj.as<MixJob>(), (int)m.jobs.size(), m.max_elems, m.dt.as<MixTerm>(), in, (__nv_bfloat16*)out, st);
+}
+
+// ------------------------------------------------------------------------------------------
+// Small helper kernels local to this file
+// ------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_scale_plain(double* x, long long n, double s) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] *= s;
+}
+
+// out block (rows x cols, row-major) = in block with column c scaled by v[voff + c].
+struct ColScaleJob { long long src, dst, voff; int rows, cols; };
+__global__ void k_colscale(const ColScaleJob* jobs, const double* in, const double* v, double* out) {
+    const ColScaleJob j = jobs[blockIdx.y];
+    long long total = (long long)j.rows * j.cols;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(e % j.cols);
+        out[j.dst + e] = in[j.src + e] * v[j.voff + c];
+    }
+}
+
+// SVD scatter: write kept singular vectors into packed site-tensor blocks.
+struct ScatJob {
+    long long dst;       // output block offset
+    long long base;      // W or V sector base offset
+    long long s_off;     // sector offset into sig/order
+    int rows, cols;      // output block shape
+    int ld;              // column length of the source matrix (W: p, V: n)
+    int off0;            // row offset inside the source column (r0 or c0)
+    int fromW;           // 1: source columns in W (divide by sigma), 0: in V
+    int left;            // 1: output [a][t] (t = kept index = column), 0: output [t][c]
+    int lam_pow;         // multiply by lambda_t (normalised) when 1
+    int pad_;
+};
+__global__ void k_svd_scatter(const ScatJob* jobs, const double* W, const double* V, const double* sig,
+                              const int* order, const double* weights, double* out) {
+    const ScatJob j = jobs[blockIdx.y];
+    const double nrm = sqrt(weights[1]);
+    long long total = (long long)j.rows * j.cols;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e / j.cols), c = (int)(e % j.cols);
+        int t = j.left ? c : r;          // kept index
+        int x = j.left ? r : c;          // position inside the source column
+        int col = order[j.s_off + t];
+        double sg = sig[j.s_off + col];
+        double val = j.fromW ? W[j.base + (long long)col * j.ld + j.off0 + x] / sg
+                             : V[j.base + (long long)col * j.ld + j.off0 + x];
+        if (j.lam_pow) val *= sg / nrm;
+        out[j.dst + e] = val;
+    }
+}
+
+// lam_out[o + t] = sig[s_off + order[s_off + t]] / nrm
+struct LamJob { long long s_off, o; int k, pad_; };
+__global__ void k_lam_out(const LamJob* jobs, int njobs, const double* sig, const int* order, const double* weights,
+                          double* lam) {
+    const double nrm = sqrt(weights[1]);
+    for (int b = blockIdx.x; b < njobs; b += gridDim.x) {
+        LamJob j = jobs[b];
+        for (int t = threadIdx.x; t < j.k; t += blockDim.x) lam[j.o + t] = sig[j.s_off + order[j.s_off + t]] / nrm;
+    }
+}
+
+__global__ void k_place(double* G, int ldg, int k, const double* col, const double* row) {
+    // G[i*ldg + k] = col[i] (i <= k);  G[k*ldg + i] = row[i] (i < k)
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+        G[(long long)i * ldg + k] = col[i];
+        if (i < k) G[(long long)k * ldg + i] = row[i];
+    }
+}
+
+inline int gridn(long long n, int cap = 2048) {
+    long long g = (n + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(g, cap));
+}
+
+}  // namespace
+
+namespace {
+struct RCJob { long long off, voff; int rows, cols, by_col, pad_; };
+__global__ void k_rcscale(const RCJob* jobs, const double* in, const double* v, double* out) {
+    const RCJob j = jobs[blockIdx.y];
+    long long total = (long long)j.rows * j.cols;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e / j.cols), c = (int)(e % j.cols);
+        out[j.off + e] = in[j.off + e] * v[j.voff + (j.by_col ? c : r)];
+    }
+}
+}  // namespace
+
+void scale_site(const Sec& bl, const Sec& br, const std::vector<int>& qn, const double* in, const double* lam,
+                bool right_index, double* out, cudaStream_t st) {
+    const SiteLayout S = site_layout(bl, br, qn);
+    const Sec& vb = right_index ? br : bl;
+    std::vector<long long> voff(vb.n() + 1, 0);
+    for (int i = 0; i < vb.n(); ++i) voff[i + 1] = voff[i] + vb.m[i];
+    std::vector<RCJob> jobs;
+    int mx = 1;
+    for (const auto& b : S.blk) {
+        jobs.push_back({b.off, voff[right_index ? b.j : b.i], b.rows, b.cols, right_index ? 1 : 0, 0});
+        mx = std::max(mx, b.rows * b.cols);
+    }
+    if (jobs.empty()) return;
+    DBuf dj;
+    upload(dj, jobs, st);
+    k_rcscale<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<RCJob>(), in, lam, out);
+    PD_CK(cudaGetLastError());
+    PD_CK(cudaStreamSynchronize(st));
+}
+
+void scale_vec(double* x, long long n, double s, cudaStream_t st) {
+    if (n <= 0) return;
+    k_scale_plain<<<gridn(n), 256, 0, st>>>(x, n, s);
+    PD_CK(cudaGetLastError());
+}
+
+double dot_host(const double* x, const double* y, long long n, cudaStream_t st) {
+    DBuf part, out;
+    int nch = 64;
+    part.ensure(sizeof(double) * nch, st);
+    out.ensure(sizeof(double), st);
+    launch_dots(x, 0, 1, y, n, part.as<double>(), nch, out.as<double>(), st);
+    double h = 0.0;
+    PD_CK(cudaMemcpyAsync(&h, out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    return h;
+}
+
+// ------------------------------------------------------------------------------------------
+// Projected Hamiltonian plan: out = L x W1 x W2 x R applied to psi
+// ------------------------------------------------------------------------------------------
+std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std::vector<int>& qn,
+                                         const TwoSiteMPO& w12, const EnvLayout& L, const EnvLayout& R,
+                                         int prec, cudaStream_t st) {
+    auto P = std::make_unique<HeffPlan>();
+    const int d = (int)qn.size();
+    P->prec = prec;
+    P->psi = psi_layout(bl, br, qn);
+    P->L = &L;
+    P->R = &R;
+    P->ld_psi = pad_ld(bl.maxm(), prec);
+    P->ld_y = pad_ld(br.maxm(), prec);
+    PD_REQUIRE(L.ld == pad_ld(bl.maxm(), prec) && R.ld == pad_ld(br.maxm(), prec), DMRG_ERR_STATE,
+               "environment slab stride does not match the bond");
+    const auto& pb = P->psi.blk;
+    const int nb = (int)pb.size();
+
+    // pack x (canonical [a][c]) into the transposed operand slab psiT ([c][a] rows)
+    std::vector<long long> prow(nb);
+    long long row = 0;
+    for (int b = 0; b < nb; ++b) {
+        prow[b] = row;
+        CopyJob j{};
+        j.src = pb[b].off; j.dst = row * P->ld_psi;
+        j.rows = pb[b].cols; j.cols = pb[b].rows;
+        j.srs = 1; j.scs = pb[b].cols; j.drs = P->ld_psi; j.dcs = 1;
+        j.zero_to = kpad(pb[b].rows, prec); j.scale = 1.0;
+        P->pack.add(j);
+        row += pb[b].cols;
+    }
+    P->psiT_rows = row;
+
+    // which (w, s1', s2') combinations feed anything
+    std::vector<char> used((size_t)w12.D0 * d * d, 0);
+    for (const auto& e : w12.nz) used[((size_t)e.w * d + e.s1p) * d + e.s2p] = 1;
+
+    // L stage: X[w, b] = L_w psi_b, X block [a_bra][c]
+    struct XB { long long off; int rows, cols, iab; };
+    std::map<std::pair<int, int>, XB> xb;   // (w, b)
+    long long xoff = 0;
+    for (int b = 0; b < nb; ++b) {
+        const auto& B = pb[b];
+        for (int w = 0; w < w12.D0; ++w) {
+            if (!used[((size_t)w * d + B.s1) * d + B.s2]) continue;
+            int iab = bl.find(bl.q[B.i] + w12.f0[w]);
+            if (iab < 0) continue;
+            int lb = L.at(iab, w);
+            if (lb < 0) continue;
+            XB x{xoff, bl.m[iab], B.cols, iab};
+            xb[{w, b}] = x;
+            GSeg sg{prow[b] * P->ld_psi, L.blk[lb].row * L.ld, B.rows, 0};
+            P->lstage.add(B.cols, bl.m[iab], xoff, P->ld_psi, 1, L.ld, 1, 1, B.cols, {sg});
+            xoff += (long long)x.rows * x.cols;
+        }
+    }
+    P->x_size = xoff;
+
+    // MPO mix: Y[w2, o] = sum coef X[w, b]   (o = output block (iab, s1, s2))
+    std::map<std::pair<int, int>, std::vector<std::pair<const XB*, double>>> yterms;   // (o, w2)
+    for (const auto& e : w12.nz) {
+        for (int b = 0; b < nb; ++b) {
+            const auto& B = pb[b];
+            if (B.s1 != e.s1p || B.s2 != e.s2p) continue;
+            auto it = xb.find({e.w, b});
+            if (it == xb.end()) continue;
+            int o = P->psi.at(it->second.iab, e.s1, e.s2);
+            if (o < 0) continue;
+            int rb = R.at(pb[o].k, e.w2);
+            if (rb < 0) continue;
+            PD_REQUIRE(R.blk[rb].k == B.k, DMRG_ERR_QN, "MPO flux rule violated in the two-site operator");
+            yterms[{o, e.w2}].push_back({&it->second, e.v});
+        }
+    }
+    // Y slab rows and R-stage segments per output block
+    std::map<int, std::vector<GSeg>> rsegs;
+    long long yrow = 0;
+    for (auto& kv : yterms) {
+        int o = kv.first.first, w2 = kv.first.second;
+        const XB* x0 = kv.second.front().first;
+        MixJob mj{};
+        mj.dst = yrow * P->ld_y;
+        mj.rows = x0->rows;
+        mj.cols = x0->cols;
+        mj.ldo = P->ld_y;
+        mj.zero_to = kpad(x0->cols, prec);
+        mj.t0 = (int)P->mix.terms.size();
+        mj.nt = (int)kv.second.size();
+        for (auto& t : kv.second) P->mix.terms.push_back({t.first->off, t.first->cols, 0, t.second});
+        P->mix.jobs.push_back(mj);
+        P->mix.max_elems = std::max(P->mix.max_elems, mj.rows * std::max(mj.cols, mj.zero_to));
+        P->mix.flops += 2.0 * mj.rows * mj.cols * mj.nt;
+        int rb = R.at(pb[o].k, w2);
+        rsegs[o].push_back({R.blk[rb].row * R.ld, yrow * P->ld_y, x0->cols, 0});
+        yrow += x0->rows;
+    }
+    P->y_rows = yrow;
+    for (auto& kv : rsegs) {
+        const auto& O = pb[kv.first];
+        P->rstage.add(O.cols, O.rows, O.off, R.ld, 1, P->ld_y, 1, 1, O.cols, kv.second);
+    }
+
+    // diagonal
+    for (int b = 0; b < nb; ++b) {
+        const auto& B = pb[b];
+        DiagJob j{};
+        j.off = B.off; j.rows = B.rows; j.cols = B.cols; j.t0 = (int)P->dterms.size(); j.nt = 0;
+        for (const auto& e : w12.nz) {
+            if (e.s1 != B.s1 || e.s1p != B.s1 || e.s2 != B.s2 || e.s2p != B.s2) continue;
+            if (w12.f0[e.w] != 0 || w12.f2[e.w2] != 0) continue;
+            int lb = L.at(B.i, e.w), rb = R.at(B.k, e.w2);
+            if (lb < 0 || rb < 0) continue;
+            P->dterms.push_back({L.blk[lb].row * L.ld, R.blk[rb].row * R.ld, e.v});
+            ++j.nt;
+        }
+        P->djobs.push_back(j);
+        P->diag_max = std::max(P->diag_max, B.rows * B.cols);
+    }
+
+    P->flops = P->lstage.flops + P->rstage.flops + P->mix.flops;
+    // upload static lists
+    P->pack.up(st);
+    P->mix.up(st);
+    upload(P->ddj, P->djobs, st);
+    upload(P->ddt, P->dterms, st);
+    const Num t = mv_num(prec);
+    P->psiT.ensure(std::max<long long>(1, P->psiT_rows) * P->ld_psi * num_size(t), st);
+    P->Y.ensure(std::max<long long>(1, P->y_rows) * P->ld_y * num_size(t), st);
+    P->X.ensure(std::max<long long>(1, P->x_size) * (prec == DMRG_FP64 ? 8 : 4), st);
+    return P;
+}
+
+static const void* env_operand(const EnvSlab& e, int prec) {
+    if (prec == DMRG_BF16) {
+        PD_REQUIRE(e.op_valid, DMRG_ERR_STATE, "bf16 operand copy of an environment is stale");
+        return e.op.p;
+    }
+    return e.buf.p;
+}
+
+void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x, double* y,
+                unsigned* err, cudaStream_t st) {
+    const int prec = P.prec;
+    const Num t = mv_num(prec);
+    run_copy<double>(P.pack, x, P.psiT.p, t, st);
+    PD_CK(cudaMemsetAsync(y, 0, sizeof(double) * std::max<long long>(P.psi.size, 1), st));
+    if (prec == DMRG_FP64) {
+        run_gemm64(P.lstage, P.psiT.as<double>(), L.buf.as<double>(), P.X.as<double>(), st);
+        run_mix<double>(P.mix, P.X.as<double>(), P.Y.p, Num::F64, st);
+        run_gemm64(P.rstage, R.buf.as<double>(), P.Y.as<double>(), y, st);
+    } else {
+        run_gemm_tc(P.lstage, t, P.psiT.p, P.psiT_rows, P.ld_psi, env_operand(L, prec), L.lay.rows, L.lay.ld,
+                    P.X.p, false, err, st);
+        run_mix<float>(P.mix, P.X.as<float>(), P.Y.p, t, st);
+        run_gemm_tc(P.rstage, t, env_operand(R, prec), R.lay.rows, R.lay.ld, P.Y.p, P.y_rows, P.ld_y, y, true, err, st);
+    }
+}
+
+void heff_diag(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* out, cudaStream_t st) {
+    if (P.djobs.empty()) return;
+    if (L.num == Num::F64)
+        launch_diag<double>(P.ddj.as<DiagJob>(), (int)P.djobs.size(), P.diag_max, P.ddt.as<DiagTerm>(),
+                            L.buf.as<double>(), L.lay.ld, R.buf.as<double>(), R.lay.ld, out, st);
+    else
+        launch_diag<float>(P.ddj.as<DiagJob>(), (int)P.djobs.size(), P.diag_max, P.ddt.as<DiagTerm>(),
+                           L.buf.as<float>(), L.lay.ld, R.buf.as<float>(), R.lay.ld, out, st);
+}
+
+// ------------------------------------------------------------------------------------------
+// Environment slabs
+// ------------------------------------------------------------------------------------------
+void env_alloc(EnvSlab& e, const Sec& b, const std::vector<int>& flux, int prec, cudaStream_t st) {
+    e.lay = env_layout(b, flux, pad_ld(b.maxm(), prec));
+    e.num = env_num(prec);
+    size_t bytes = (size_t)std::max<long long>(1, e.lay.rows) * e.lay.ld * num_size(e.num);
+    e.buf.ensure(bytes, st);
+    PD_CK(cudaMemsetAsync(e.buf.p, 0, bytes, st));
+    e.op_valid = false;
+    e.valid = true;
+}
+
+void env_make_operand(EnvSlab& e, int prec, cudaStream_t st) {
+    if (prec != DMRG_BF16 || e.op_valid) return;
+    CopyList c;
+    long long n = std::max<long long>(1, e.lay.rows) * e.lay.ld;
+    // one flat row-major copy of the whole slab (padding included, zeros stay zeros)
+    const long long chunk = 1 << 20;
+    for (long long s = 0; s < n; s += chunk) {
+        CopyJob j{};
+        j.src = s; j.dst = s; j.rows = 1; j.cols = (int)std::min(chunk, n - s);
+        j.srs = 0; j.scs = 1; j.drs = 0; j.dcs = 1; j.zero_to = 0; j.scale = 1.0;
+        c.add(j);
+    }
+    c.up(st);
+    e.op.ensure(n * 2, st);
+    run_copy<float>(c, e.buf.as<float>(), e.op.p, Num::BF16, st);
+    e.op_valid = true;
+}
+
+void env_from_packed(EnvSlab& e, const double* packed, cudaStream_t st) {
+    CopyList c;
+    for (const auto& b : e.lay.blk) {
+        CopyJob j{};
+        j.src = b.packed; j.dst = b.row * e.lay.ld; j.rows = b.rows; j.cols = b.cols;
+        j.srs = b.cols; j.scs = 1; j.drs = e.lay.ld; j.dcs = 1; j.zero_to = 0; j.scale = 1.0;
+        c.add(j);
+    }
+    c.up(st);
+    run_copy<double>(c, packed, e.buf.p, e.num, st);
+    e.op_valid = false;
+    e.valid = true;
+}
+
+void env_to_packed(const EnvSlab& e, double* packed, cudaStream_t st) {
+    CopyList c;
+    for (const auto& b : e.lay.blk) {
+        CopyJob j{};
+        j.src = b.row * e.lay.ld; j.dst = b.packed; j.rows = b.rows; j.cols = b.cols;
+        j.srs = e.lay.ld; j.scs = 1; j.drs = b.cols; j.dcs = 1; j.zero_to = 0; j.scale = 1.0;
+        c.add(j);
+    }
+    c.up(st);
+    if (e.num == Num::F64) run_copy<double>(c, e.buf.as<double>(), packed, Num::F64, st);
+    else run_copy<float>(c, e.buf.as<float>(), packed, Num::F64, st);
+    PD_CK(cudaStreamSynchronize(st));   // the job list is freed on return
+}
+
+void env_boundary(EnvSlab& e, const Sec& b, const std::vector<int>& flux, int prec, cudaStream_t st) {
+    env_alloc(e, b, flux, prec, st);
+    PD_REQUIRE(e.lay.blk.size() == 1 && e.lay.blk[0].rows == 1 && e.lay.blk[0].cols == 1, DMRG_ERR_QN,
+               "boundary environment is not a single 1x1 block");
+    if (e.num == Num::F64) {
+        double one = 1.0;
+        PD_CK(cudaMemcpyAsync(e.buf.p, &one, 8, cudaMemcpyHostToDevice, st));
+    } else {
+        float one = 1.0f;
+        PD_CK(cudaMemcpyAsync(e.buf.p, &one, 4, cudaMemcpyHostToDevice, st));
+    }
+    PD_CK(cudaStreamSynchronize(st));
+    e.op_valid = false;
+}
+
+// ------------------------------------------------------------------------------------------
+// Environment updates (Sec. II operator transformation)
+// ------------------------------------------------------------------------------------------
+static void run_env_gemm(GemmBatch& g, int prec, const void* A, long long arows, int lda, const void* B,
+                         long long brows, int ldb, void* C, unsigned* err, cudaStream_t st) {
+    if (g.empty()) return;
+    if (prec == DMRG_FP64) run_gemm64(g, (const double*)A, (const double*)B, (double*)C, st);
+    else run_gemm_tc(g, Num::F32, A, arows, lda, B, brows, ldb, C, false, err, st);
+}
+
+void env_update_left(const Sec& ba, const Sec& bb, const std::vector<int>& qn, const SiteMPO& W,
+                     const EnvSlab& Lin, const double* A, EnvSlab& Lout, int prec, unsigned* err, cudaStream_t st) {
+    const int d = (int)qn.size();
+    const SiteLayout S = site_layout(ba, bb, qn);
+    const EnvLayout& Li = Lin.lay;
+    const Num tn = env_num(prec);
+    const int ldS = pad_ld(ba.maxm(), prec);
+    // A^T slab: block (ia, s) rows b, cols a
+    CopyList pk;
+    std::vector<long long> srow(S.blk.size());
+    long long row = 0;
+    for (size_t b = 0; b < S.blk.size(); ++b) {
+        const auto& B = S.blk[b];
+        srow[b] = row;
+        CopyJob j{};
+        j.src = B.off; j.dst = row * ldS; j.rows = B.cols; j.cols = B.rows;
+        j.srs = 1; j.scs = B.cols; j.drs = ldS; j.dcs = 1; j.zero_to = kpad(B.rows, prec); j.scale = 1.0;
+        pk.add(j);
+        row += B.cols;
+    }
+    const long long srows = row;
+    // which (w, s') pairs feed anything
+    std::vector<char> usedws((size_t)W.Dl * d, 0);
+    for (int w = 0; w < W.Dl; ++w)
+        for (int s = 0; s < d; ++s)
+            for (int sp = 0; sp < d; ++sp)
+                for (int wp = 0; wp < W.Dr; ++wp)
+                    if (W.at(w, s, sp, wp) != 0.0) usedws[(size_t)w * d + sp] = 1;
+    // stage 1: T1(iab, w, s') [b][a_bra] = L_w A_s'
+    struct TB { long long off; int rows, cols; };   // rows = b, cols = a_bra
+    std::map<std::tuple<int, int, int>, TB> t1;
+    GemmBatch g1;
+    long long toff = 0;
+    for (const auto& lb : Li.blk) {
+        for (int sp = 0; sp < d; ++sp) {
+            if (!usedws[(size_t)lb.w * d + sp]) continue;
+            int ab = S.at(lb.k, sp);
+            if (ab < 0) continue;
+            const auto& AB = S.blk[ab];
+            TB t{toff, AB.cols, lb.rows};
+            t1[{lb.i, lb.w, sp}] = t;
+            g1.add(lb.rows, AB.cols, toff, Li.ld, 1, ldS, 1, 1, lb.rows,
+                   {GSeg{lb.row * Li.ld, srow[ab] * ldS, lb.cols, 0}});
+            toff += (long long)t.rows * t.cols;
+        }
+    }
+    // stage 2: T2(w', s, iab) [b][a_bra] = sum W[w,s,s',w'] T1(iab, w, s')
+    const EnvLayout& Lo = Lout.lay;
+    const int ldT = pad_ld(ba.maxm(), prec);
+    MixList mx;
+    std::map<std::tuple<int, int, int>, long long> t2row;
+    std::map<std::tuple<int, int, int>, std::vector<std::pair<const TB*, double>>> t2terms;
+    for (const auto& kv : t1) {
+        int iab, w, sp;
+        std::tie(iab, w, sp) = kv.first;
+        for (int s = 0; s < d; ++s)
+            for (int wp = 0; wp < W.Dr; ++wp) {
+                double c = W.at(w, s, sp, wp);
+                if (c == 0.0) continue;
+                if (S.at(iab, s) < 0) continue;
+                int ibb = bb.find(ba.q[iab] + qn[s]);
+                if (ibb < 0 || Lo.at(ibb, wp) < 0) continue;
+                t2terms[{wp, s, iab}].push_back({&kv.second, c});
+            }
+    }
+    long long trow = 0;
+    for (auto& kv : t2terms) {
+        const TB* x0 = kv.second.front().first;
+        t2row[kv.first] = trow;
+        MixJob mj{};
+        mj.dst = trow * ldT; mj.rows = x0->rows; mj.cols = x0->cols; mj.ldo = ldT;
+        mj.zero_to = kpad(x0->cols, prec); mj.t0 = (int)mx.terms.size(); mj.nt = (int)kv.second.size();
+        for (auto& t : kv.second) mx.terms.push_back({t.first->off, t.first->cols, 0, t.second});
+        mx.jobs.push_back(mj);
+        mx.max_elems = std::max(mx.max_elems, mj.rows * std::max(mj.cols, mj.zero_to));
+        trow += x0->rows;
+    }
+    // stage 3: Lout(ibb, w') [b_bra][b] = sum_{s, iab} A_s^T T2(w', s, iab)
+    GemmBatch g3;
+    for (const auto& ob : Lo.blk) {
+        std::vector<GSeg> sg;
+        for (int s = 0; s < d; ++s) {
+            int iab = ba.find(bb.q[ob.i] - qn[s]);
+            if (iab < 0) continue;
+            int ab = S.at(iab, s);
+            if (ab < 0) continue;
+            auto it = t2row.find({ob.w, s, iab});
+            if (it == t2row.end()) continue;
+            sg.push_back({it->second * ldT, srow[ab] * ldS, ba.m[iab], 0});
+        }
+        g3.add(ob.cols, ob.rows, ob.row * Lo.ld, ldT, 1, ldS, 1, 1, Lo.ld, sg);
+    }
+    // execute
+    pk.up(st);
+    mx.up(st);
+    DBuf sl, t1b, t2b;
+    sl.ensure(std::max<long long>(1, srows) * ldS * num_size(tn), st);
+    t1b.ensure(std::max<long long>(1, toff) * num_size(tn), st);
+    t2b.ensure(std::max<long long>(1, trow) * ldT * num_size(tn), st);
+    run_copy<double>(pk, A, sl.p, tn, st);
+    run_env_gemm(g1, prec, Lin.buf.p, Li.rows, Li.ld, sl.p, srows, ldS, t1b.p, err, st);
+    if (tn == Num::F64) run_mix<double>(mx, t1b.as<double>(), t2b.p, tn, st);
+    else run_mix<float>(mx, t1b.as<float>(), t2b.p, tn, st);
+    run_env_gemm(g3, prec, t2b.p, trow, ldT, sl.p, srows, ldS, Lout.buf.p, err, st);
+    Lout.op_valid = false;
+    PD_CK(cudaStreamSynchronize(st));   // scratch and job lists are released on return
+}
+
+void env_update_right(const Sec& ba, const Sec& bc, const std::vector<int>& qn, const SiteMPO& W,
+                      const EnvSlab& Rin, const double* Bt, EnvSlab& Rout, int prec, unsigned* err, cudaStream_t st) {
+    const int d = (int)qn.size();
+    const SiteLayout S = site_layout(ba, bc, qn);
+    const EnvLayout& Ri = Rin.lay;
+    const Num tn = env_num(prec);
+    const int ldS = pad_ld(bc.maxm(), prec);
+    // B slab: block (ia, s) rows a, cols c (same orientation as the packed block)
+    CopyList pk;
+    std::vector<long long> srow(S.blk.size());
+    long long row = 0;
+    for (size_t b = 0; b < S.blk.size(); ++b) {
+        const auto& B = S.blk[b];
+        srow[b] = row;
+        CopyJob j{};
+        j.src = B.off; j.dst = row * ldS; j.rows = B.rows; j.cols = B.cols;
+        j.srs = B.cols; j.scs = 1; j.drs = ldS; j.dcs = 1; j.zero_to = kpad(B.cols, prec); j.scale = 1.0;
+        pk.add(j);
+        row += B.rows;
+    }
+    const long long srows = row;
+    std::vector<char> usedws((size_t)W.Dr * d, 0);   // (w', s')
+    for (int w = 0; w < W.Dl; ++w)
+        for (int s = 0; s < d; ++s)
+            for (int sp = 0; sp < d; ++sp)
+                for (int wp = 0; wp < W.Dr; ++wp)
+                    if (W.at(w, s, sp, wp) != 0.0) usedws[(size_t)wp * d + sp] = 1;
+    // stage 1: T1(icb, w', s') [a][c_bra] = R_w' B_s'^T
+    struct TB { long long off; int rows, cols; };   // rows = a, cols = c_bra
+    std::map<std::tuple<int, int, int>, TB> t1;
+    GemmBatch g1;
+    long long toff = 0;
+    for (const auto& rb : Ri.blk) {
+        for (int sp = 0; sp < d; ++sp) {
+            if (!usedws[(size_t)rb.w * d + sp]) continue;
+            int ia = ba.find(bc.q[rb.k] - qn[sp]);
+            if (ia < 0) continue;
+            int bbk = S.at(ia, sp);
+            if (bbk < 0) continue;
+            const auto& BB = S.blk[bbk];
+            TB t{toff, BB.rows, rb.rows};
+            t1[{rb.i, rb.w, sp}] = t;
+            g1.add(rb.rows, BB.rows, toff, Ri.ld, 1, ldS, 1, 1, rb.rows,
+                   {GSeg{rb.row * Ri.ld, srow[bbk] * ldS, rb.cols, 0}});
+            toff += (long long)t.rows * t.cols;
+        }
+    }
+    // stage 2: T2(w, s, icb) [a][c_bra] = sum W[w,s,s',w'] T1(icb, w', s')
+    const EnvLayout& Ro = Rout.lay;
+    const int ldT = pad_ld(bc.maxm(), prec);
+    MixList mx;
+    std::map<std::tuple<int, int, int>, long long> t2row;
+    std::map<std::tuple<int, int, int>, std::vector<std::pair<const TB*, double>>> t2terms;
+    for (const auto& kv : t1) {
+        int icb, wp, sp;
+        std::tie(icb, wp, sp) = kv.first;
+        for (int w = 0; w < W.Dl; ++w)
+            for (int s = 0; s < d; ++s) {
+                double c = W.at(w, s, sp, wp);
+                if (c == 0.0) continue;
+                int iab = ba.find(bc.q[icb] - qn[s]);
+                if (iab < 0 || S.at(iab, s) < 0) continue;
+                if (Ro.at(iab, w) < 0) continue;
+                t2terms[{w, s, icb}].push_back({&kv.second, c});
+            }
+    }
+    long long trow = 0;
+    for (auto& kv : t2terms) {
+        const TB* x0 = kv.second.front().first;
+        t2row[kv.first] = trow;
+        MixJob mj{};
+        mj.dst = trow * ldT; mj.rows = x0->rows; mj.cols = x0->cols; mj.ldo = ldT;
+        mj.zero_to = kpad(x0->cols, prec); mj.t0 = (int)mx.terms.size(); mj.nt = (int)kv.second.size();
+        for (auto& t : kv.second) mx.terms.push_back({t.first->off, t.first->cols, 0, t.second});
+        mx.jobs.push_back(mj);
+        mx.max_elems = std::max(mx.max_elems, mj.rows * std::max(mj.cols, mj.zero_to));
+        trow += x0->rows;
+    }
+    // stage 3: Rout(iab, w) [a_bra][a] = sum_{s, icb} B_s T2(w, s, icb)^T
+    GemmBatch g3;
+    for (const auto& ob : Ro.blk) {
+        std::vector<GSeg> sg;
+        for (int s = 0; s < d; ++s) {
+            int icb = bc.find(ba.q[ob.i] + qn[s]);
+            if (icb < 0) continue;
+            int bbk = S.at(ob.i, s);
+            if (bbk < 0) continue;
+            auto it = t2row.find({ob.w, s, icb});
+            if (it == t2row.end()) continue;
+            sg.push_back({it->second * ldT, srow[bbk] * ldS, bc.m[icb], 0});
+        }
+        g3.add(ob.cols, ob.rows, ob.row * Ro.ld, ldT, 1, ldS, 1, 1, Ro.ld, sg);
+    }
+    pk.up(st);
+    mx.up(st);
+    DBuf sl, t1b, t2b;
+    sl.ensure(std::max<long long>(1, srows) * ldS * num_size(tn), st);
+    t1b.ensure(std::max<long long>(1, toff) * num_size(tn), st);
+    t2b.ensure(std::max<long long>(1, trow) * ldT * num_size(tn), st);
+    run_copy<double>(pk, Bt, sl.p, tn, st);
+    run_env_gemm(g1, prec, Rin.buf.p, Ri.rows, Ri.ld, sl.p, srows, ldS, t1b.p, err, st);
+    if (tn == Num::F64) run_mix<double>(mx, t1b.as<double>(), t2b.p, tn, st);
+    else run_mix<float>(mx, t1b.as<float>(), t2b.p, tn, st);
+    run_env_gemm(g3, prec, t2b.p, trow, ldT, sl.p, srows, ldS, Rout.buf.p, err, st);
+    Rout.op_valid = false;
+    PD_CK(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------------------------------
+// Two-site wavefunction from site tensors
+// ------------------------------------------------------------------------------------------
+void form_two_site(const Sec& bl, const Sec& bm, const Sec& br, const std::vector<int>& qn, const double* left,
+                   const double* right, const double* mid, double* psi, cudaStream_t st) {
+    const int d = (int)qn.size();
+    const SiteLayout SL = site_layout(bl, bm, qn);
+    const SiteLayout SR = site_layout(bm, br, qn);
+    const PsiLayout P = psi_layout(bl, br, qn);
+    DBuf scaled;
+    const double* lsrc = left;
+    if (mid) {
+        // left' = left with its middle (column) index scaled by mid
+        std::vector<long long> moff(bm.n() + 1, 0);
+        for (int i = 0; i < bm.n(); ++i) moff[i + 1] = moff[i] + bm.m[i];
+        std::vector<ColScaleJob> jobs;
+        int mx = 1;
+        for (const auto& b : SL.blk) {
+            jobs.push_back({b.off, b.off, moff[b.j], b.rows, b.cols});
+            mx = std::max(mx, b.rows * b.cols);
+        }
+        DBuf dj;
+        upload(dj, jobs, st);
+        scaled.ensure(std::max<long long>(1, SL.size) * 8, st);
+        if (!jobs.empty()) {
+            k_colscale<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<ColScaleJob>(), left, mid,
+                                                                                   scaled.as<double>());
+            PD_CK(cudaGetLastError());
+        }
+        lsrc = scaled.as<double>();
+        PD_CK(cudaStreamSynchronize(st));
+    }
+    GemmBatch g;
+    for (const auto& b : P.blk) {
+        int im = bm.find(bl.q[b.i] + qn[b.s1]);
+        if (im < 0) continue;
+        int lb = SL.at(b.i, b.s1), rb = SR.at(im, b.s2);
+        if (lb < 0 || rb < 0) continue;
+        // C(m = c, n = a) = sum_mid right[mid][c] left[a][mid]
+        g.add(b.cols, b.rows, b.off, 1, b.cols, bm.m[im], 1, 1, b.cols,
+              {GSeg{SR.blk[rb].off, SL.blk[lb].off, bm.m[im], 0}});
+    }
+    PD_CK(cudaMemsetAsync(psi, 0, sizeof(double) * std::max<long long>(1, P.size), st));
+    (void)d;
+    run_gemm64(g, right, lsrc, psi, st);
+    PD_CK(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------------------------------
+// SVD split with truncation (Eq. svd)
+// ------------------------------------------------------------------------------------------
+namespace {
+struct SecInfo {
+    int qm = 0;
+    std::map<std::pair<int, int>, int> roff, coff;   // (i, s1) -> row offset, (s2, k) -> col offset
+    int r = 0, c = 0;
+};
+std::map<int, SecInfo> split_sectors(const PsiLayout& P, const Sec& bl, const Sec& br, const std::vector<int>& qn1) {
+    std::map<int, SecInfo> secs;
+    for (const auto& b : P.blk) {
+        int qm = bl.q[b.i] + qn1[b.s1];
+        auto& S = secs[qm];
+        S.qm = qm;
+        S.roff[{b.i, b.s1}] = 0;
+        S.coff[{b.s2, b.k}] = 0;
+    }
+    for (auto& kv : secs) {
+        auto& S = kv.second;
+        int o = 0;
+        for (auto& r : S.roff) { r.second = o; o += bl.m[r.first.first]; }
+        S.r = o;
+        o = 0;
+        for (auto& c : S.coff) { c.second = o; o += br.m[c.first.second]; }
+        S.c = o;
+    }
+    return secs;
+}
+}  // namespace
+
+void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
+                      long long* a_elems, long long* b_elems, long long* lam_elems) {
+    const PsiLayout P = psi_layout2(bl, br, qn1, qn2);
+    auto secs = split_sectors(P, bl, br, qn1);
+    long long a = 0, b = 0, l = 0;
+    for (auto& kv : secs) {
+        long long k = std::min(kv.second.r, kv.second.c);
+        a += (long long)kv.second.r * k;
+        b += k * kv.second.c;
+        l += k;
+    }
+    *a_elems = a;
+    *b_elems = b;
+    *lam_elems = l;
+}
+
+SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
+                      const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
+                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st) {
+    (void)accurate;
+    const PsiLayout P = psi_layout2(bl, br, qn1, qn2);
+    const std::vector<int>& qn = qn1;
+    // sector layout: rows (i, s1) sorted, cols (s2, k) sorted, per middle charge
+    auto secs = split_sectors(P, bl, br, qn1);
+    std::vector<SecInfo*> order_secs;
+    for (auto& kv : secs) order_secs.push_back(&kv.second);
+    const int nsec = (int)order_secs.size();
+    std::vector<SvdSec> ss(nsec);
+    std::vector<int> pair_sec;
+    long long woff = 0, voff = 0, soff = 0;
+    int maxn = 0, maxnpad = 0, maxp = 1;
+    for (int s = 0; s < nsec; ++s) {
+        auto& S = *order_secs[s];
+        SvdSec x{};
+        x.p = std::max(S.r, S.c);
+        x.n = std::min(S.r, S.c);
+        x.npad = x.n + (x.n & 1);
+        x.w_off = woff; x.v_off = voff; x.s_off = soff;
+        x.pair0 = (int)pair_sec.size();
+        for (int i = 0; i < x.npad / 2; ++i) pair_sec.push_back(s);
+        woff += (long long)x.p * x.n;
+        voff += (long long)x.n * x.n;
+        soff += x.n;
+        maxn = std::max(maxn, x.n);
+        maxp = std::max(maxp, x.p);
+        maxnpad = std::max(maxnpad, x.npad);
+        ss[s] = x;
+    }
+    const int total = (int)soff;
+    // gather Psi blocks into W
+    CopyList gather;
+    for (const auto& b : P.blk) {
+        int qm = bl.q[b.i] + qn[b.s1];
+        int s = (int)(std::find_if(order_secs.begin(), order_secs.end(), [&](SecInfo* x) { return x->qm == qm; }) - order_secs.begin());
+        const auto& S = *order_secs[s];
+        int r0 = S.roff.at({b.i, b.s1}), c0 = S.coff.at({b.s2, b.k});
+        CopyJob j{};
+        j.src = b.off; j.rows = b.rows; j.cols = b.cols; j.srs = b.cols; j.scs = 1; j.zero_to = 0; j.scale = 1.0;
+        if (S.r >= S.c) {   // W = M, column-major r x c
+            j.dst = ss[s].w_off + (long long)c0 * S.r + r0; j.drs = 1; j.dcs = S.r;
+        } else {            // W = M^T, column-major c x r
+            j.dst = ss[s].w_off + (long long)r0 * S.c + c0; j.drs = S.c; j.dcs = 1;
+        }
+        gather.add(j);
+    }
+    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts;
+    dW.ensure(std::max<long long>(1, woff) * 8, st);
+    dV.ensure(std::max<long long>(1, voff) * 8, st);
+    dsig.ensure(std::max<long long>(1, soff) * 8, st);
+    dord.ensure(std::max<long long>(1, soff) * 4, st);
+    dkept.ensure(std::max(1, nsec) * 4, st);
+    dwts.ensure(16, st);
+    drot.ensure(4, st);
+    upload(dsecs, ss, st);
+    upload(dpairs, pair_sec, st);
+    gather.up(st);
+    PD_CK(cudaMemsetAsync(dW.p, 0, std::max<long long>(1, woff) * 8, st));
+    run_copy<double>(gather, psi, dW.p, Num::F64, st);
+    launch_svd_init_v(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
+    const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+    const int npairs = (int)pair_sec.size();
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        PD_CK(cudaMemsetAsync(drot.p, 0, 4, st));
+        for (int round = 0; round < maxnpad - 1; ++round)
+            launch_jacobi_round(dsecs.as<SvdSec>(), dpairs.as<int>(), npairs, round, dW.as<double>(),
+                                dV.as<double>(), tol, drot.as<int>(), st);
+        int rot = 0;
+        PD_CK(cudaMemcpyAsync(&rot, drot.p, 4, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+        if (!rot) break;
+    }
+    launch_svd_finish(dsecs.as<SvdSec>(), nsec, maxn, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
+    launch_truncate(dsecs.as<SvdSec>(), nsec, dsig.as<double>(), dord.as<int>(), total, m_max, rel_cutoff, 1e-10,
+                    dkept.as<int>(), dwts.as<double>(), st);
+    std::vector<int> kept(nsec);
+    double wts[2];
+    PD_CK(cudaMemcpyAsync(kept.data(), dkept.p, 4 * nsec, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(wts, dwts.p, 16, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    SplitResult res;
+    std::vector<int> kept_of_sec(nsec, 0);
+    for (int s = 0; s < nsec; ++s)
+        if (kept[s] > 0) {
+            res.mid.q.push_back(order_secs[s]->qm);
+            res.mid.m.push_back(kept[s]);
+            kept_of_sec[s] = kept[s];
+        }
+    PD_REQUIRE(res.mid.n() > 0, DMRG_ERR_NUMERIC, "SVD kept no singular value (zero wavefunction?)");
+    res.trunc = wts[0] > 0 ? std::max(0.0, (wts[0] - wts[1]) / wts[0]) : 0.0;
+    // scatter
+    const SiteLayout SA = site_layout(bl, res.mid, qn1);
+    const SiteLayout SB = site_layout(res.mid, br, qn2);
+    std::vector<ScatJob> jobs;
+    int mx = 1;
+    for (int s = 0; s < nsec; ++s) {
+        if (!kept_of_sec[s]) continue;
+        const auto& S = *order_secs[s];
+        int im = res.mid.find(S.qm);
+        bool rge = S.r >= S.c;
+        for (const auto& r : S.roff) {        // A blocks (i, s1) [a][k]
+            int ab = SA.at(r.first.first, r.first.second);
+            if (ab < 0) continue;
+            ScatJob j{};
+            j.dst = SA.blk[ab].off; j.rows = SA.blk[ab].rows; j.cols = SA.blk[ab].cols;
+            j.s_off = ss[s].s_off; j.off0 = r.second; j.left = 1; j.lam_pow = lam_pow_left;
+            if (rge) { j.fromW = 1; j.base = ss[s].w_off; j.ld = ss[s].p; }
+            else { j.fromW = 0; j.base = ss[s].v_off; j.ld = ss[s].n; }
+            jobs.push_back(j);
+            mx = std::max(mx, j.rows * j.cols);
+        }
+        for (const auto& c : S.coff) {        // B blocks (m, s2) [k][c]
+            int bb = SB.at(im, c.first.first);
+            if (bb < 0) continue;
+            ScatJob j{};
+            j.dst = SB.blk[bb].off + 0; j.rows = SB.blk[bb].rows; j.cols = SB.blk[bb].cols;
+            j.s_off = ss[s].s_off; j.off0 = c.second; j.left = 0; j.lam_pow = lam_pow_right;
+            if (rge) { j.fromW = 0; j.base = ss[s].v_off; j.ld = ss[s].n; }
+            else { j.fromW = 1; j.base = ss[s].w_off; j.ld = ss[s].p; }
+            // B lives in a separate buffer: mark with a negative sentinel handled below
+            j.pad_ = 1;
+            jobs.push_back(j);
+            mx = std::max(mx, j.rows * j.cols);
+        }
+    }
+    std::vector<ScatJob> ja, jb;
+    for (auto& j : jobs) (j.pad_ ? jb : ja).push_back(j);
+    DBuf dja, djb;
+    upload(dja, ja, st);
+    upload(djb, jb, st);
+    if (!ja.empty()) {
+        k_svd_scatter<<<dim3(gridn(mx, 256), (unsigned)ja.size()), 256, 0, st>>>(
+            dja.as<ScatJob>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(), dord.as<int>(), dwts.as<double>(), A_out);
+        PD_CK(cudaGetLastError());
+    }
+    if (!jb.empty()) {
+        k_svd_scatter<<<dim3(gridn(mx, 256), (unsigned)jb.size()), 256, 0, st>>>(
+            djb.as<ScatJob>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(), dord.as<int>(), dwts.as<double>(), B_out);
+        PD_CK(cudaGetLastError());
+    }
+    // lambda
+    std::vector<LamJob> lj;
+    long long o = 0;
+    for (int s = 0; s < nsec; ++s) {
+        if (!kept_of_sec[s]) continue;
+        lj.push_back({ss[s].s_off, o, kept_of_sec[s], 0});
+        o += kept_of_sec[s];
+    }
+    DBuf dlj, dlam;
+    upload(dlj, lj, st);
+    double* lam_dev = lam_out_dev;
+    if (!lam_dev) {
+        dlam.ensure(o * 8, st);
+        lam_dev = dlam.as<double>();
+    }
+    k_lam_out<<<std::max<int>(1, (int)lj.size()), 128, 0, st>>>(dlj.as<LamJob>(), (int)lj.size(), dsig.as<double>(),
+                                                                 dord.as<int>(), dwts.as<double>(), lam_dev);
+    PD_CK(cudaGetLastError());
+    res.lam.resize(o);
+    PD_CK(cudaMemcpyAsync(res.lam.data(), lam_dev, o * 8, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    return res;
+}
+
+// ------------------------------------------------------------------------------------------
+// Davidson (the Sec. II local eigensolver), FP64 vectors, same algorithm as the CPU oracle
+// ------------------------------------------------------------------------------------------
+DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, int kmax, double tol,
+                   int max_iter, unsigned* err, cudaStream_t st) {
+    const long long n = P.psi.size;
+    PD_REQUIRE(kmax >= 2 && kmax <= 32, DMRG_ERR_ARG, "Davidson kmax must be in [2, 32]");
+    DavResult res;
+    const int nch = (int)std::max<long long>(1, std::min<long long>(512, (n + 4095) / 4096));
+    DBuf dV, dAV, dG, dyth, dpart, dd1, dd2, dnrm, du, dAu, dr, dt, ddg;
+    dV.ensure((size_t)kmax * n * 8, st);
+    dAV.ensure((size_t)kmax * n * 8, st);
+    dG.ensure((size_t)kmax * kmax * 8, st);
+    dyth.ensure((kmax + 1) * 8, st);
+    dpart.ensure((size_t)std::max(2, kmax) * nch * 8, st);
+    dd1.ensure((kmax + 1) * 8, st);
+    dd2.ensure((kmax + 1) * 8, st);
+    dnrm.ensure(4 * 8, st);
+    du.ensure(n * 8, st);
+    dAu.ensure(n * 8, st);
+    dr.ensure(n * 8, st);
+    dt.ensure(n * 8, st);
+    ddg.ensure(n * 8, st);
+    double* V = dV.as<double>();
+    double* AV = dAV.as<double>();
+    double* G = dG.as<double>();
+    cudaEvent_t e0, e1;
+    PD_CK(cudaEventCreate(&e0));
+    PD_CK(cudaEventCreate(&e1));
+    auto mv = [&](const double* in, double* out) {
+        PD_CK(cudaEventRecord(e0, st));
+        heff_apply(P, L, R, in, out, err, st);
+        PD_CK(cudaEventRecord(e1, st));
+        PD_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PD_CK(cudaEventElapsedTime(&ms, e0, e1));
+        res.mv_ms += ms;
+        res.matvecs++;
+    };
+    heff_diag(P, L, R, ddg.as<double>(), st);
+    // V0 = x / |x|
+    launch_nrm2(x, n, dpart.as<double>(), nch, dnrm.as<double>(), st);
+    launch_scale(x, dnrm.as<double>(), n, V, 1, st);
+    mv(V, AV);
+    int k = 1;
+    launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
+    k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
+    PD_CK(cudaGetLastError());
+    double hn[4];
+    for (int it = 1; it <= max_iter; ++it) {
+        res.iters = it;
+        launch_small_eig(G, k, kmax, dyth.as<double>(), st);
+        launch_ritz(V, AV, n, k, dyth.as<double>(), n, du.as<double>(), dAu.as<double>(), dr.as<double>(),
+                    dpart.as<double>(), nch, dnrm.as<double>(), st);
+        PD_CK(cudaMemcpyAsync(hn, dnrm.p, 16, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaMemcpyAsync(hn + 2, dyth.p, 8, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+        res.theta = hn[2];
+        res.rnorm = std::sqrt(std::max(0.0, hn[0]));
+        PD_REQUIRE(std::isfinite(res.theta) && std::isfinite(res.rnorm), DMRG_ERR_NUMERIC,
+                   "non-finite Ritz value in Davidson");
+        if (res.rnorm <= tol * std::max(1.0, std::fabs(res.theta)) || it == max_iter) break;
+        launch_precond(dr.as<double>(), ddg.as<double>(), dyth.as<double>(), 1e-4, n, dt.as<double>(), st);
+        if (k >= kmax) {   // restart from the Ritz vector
+            launch_scale(du.as<double>(), dnrm.as<double>() + 1, n, V, 1, st);
+            launch_scale(dAu.as<double>(), dnrm.as<double>() + 1, n, AV, 1, st);
+            k = 1;
+            launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
+            k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
+            PD_CK(cudaGetLastError());
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_dots(V, n, k, dt.as<double>(), n, dpart.as<double>(), nch, dd1.as<double>(), st);
+            launch_subtract(V, n, k, dd1.as<double>(), n, dt.as<double>(), st);
+        }
+        launch_nrm2(dt.as<double>(), n, dpart.as<double>(), nch, dnrm.as<double>() + 2, st);
+        double tn2 = 0.0;
+        PD_CK(cudaMemcpyAsync(&tn2, dnrm.as<double>() + 2, 8, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+        if (std::sqrt(tn2) < 1e-14) break;
+        double* vk = V + (size_t)k * n;
+        double* avk = AV + (size_t)k * n;
+        launch_scale(dt.as<double>(), dnrm.as<double>() + 2, n, vk, 1, st);
+        mv(vk, avk);
+        // new column k: G[i][k] = V_i . AV_k (i <= k); new row: G[k][i] = V_k . AV_i (i < k)
+        launch_dots(V, n, k + 1, avk, n, dpart.as<double>(), nch, dd1.as<double>(), st);
+        launch_dots(AV, n, k, vk, n, dpart.as<double>(), nch, dd2.as<double>(), st);
+        k_place<<<1, 32, 0, st>>>(G, kmax, k, dd1.as<double>(), dd2.as<double>());
+        PD_CK(cudaGetLastError());
+        ++k;
+    }
+    // x = u / |u|
+    launch_scale(du.as<double>(), dnrm.as<double>() + 1, n, x, 1, st);
+    PD_CK(cudaStreamSynchronize(st));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return res;
+}
+
+}  // namespace pd

@@ -1,0 +1,108 @@
+"""GPU two-site DMRG (FP64 mode, C ABI) against the CPU oracle: energies, block tables and
+singular values sweep by sweep; closed-form pins; real-space regions."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import dmrg as O
+from oracle import exact
+from oracle import regions as P
+from tests._gpu import engine_for, load_mps
+
+pytestmark = pytest.mark.gpu
+pd = pytest.importorskip("paper_1301_3494_gb300")
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ed_energies.json")))
+TOL = 1e-8     # FP64 parity: |dE/E|
+
+
+def test_initial_energy_matches_oracle():
+    L = 10
+    mpo = wl.heisenberg_chain(L)
+    mps = wl.random_mps(L, mpo.site.qn, 0, 12, seed=5)
+    ref = O.SerialDMRG(mpo, mps)
+    e_ref = ref.energy_of(0, O.two_site(ref.sites[0], ref.sites[1], ref.qn))
+    eng = engine_for(pd, mpo)
+    load_mps(eng, mps, ref.qn)
+    e = eng.energy()
+    assert abs(e - e_ref) <= 1e-12 * abs(e_ref)
+    for b in range(L + 1):
+        assert eng.bond(b) == ref.bonds[b]
+
+
+def test_heisenberg_L16_m64_six_sweeps_parity():
+    """Small config: L=16, D=5, m <= 64, 6 sweeps, random normal start (seed 0)."""
+    L = 16
+    mpo = wl.heisenberg_chain(L)
+    mps = wl.random_mps(L, mpo.site.qn, 0, 64, seed=0)
+    ref = O.SerialDMRG(mpo, mps)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, mps, ref.qn)
+    for sweep in range(6):
+        r = ref.sweep(64)
+        g = eng.sweep(64, dav_tol=1e-10, dav_max_iter=100)
+        assert abs(g["energy"] - r["energy"]) <= TOL * abs(r["energy"]), sweep
+        for b in range(L + 1):
+            assert eng.bond(b) == ref.bonds[b], (sweep, b)
+    e0 = GOLD["heisenberg_chain_L16_Sz0"]
+    assert g["energy"] >= e0 - 1e-10
+    assert g["energy"] - e0 < 1e-8 * abs(e0)
+    # singular values at the centre bond
+    lam = eng.lam(8)
+    lr = np.concatenate([ref.lam[8][q] for q in sorted(ref.lam[8])])
+    assert np.abs(np.sort(lam) - np.sort(lr)).max() < 1e-8
+
+
+@pytest.mark.parametrize("h", [0.5, 1.0, 1.5])
+def test_tfim_closed_form(h):
+    L = 32
+    mpo = wl.tfim_chain(L, 1.0, h)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, wl.random_mps(L, mpo.site.qn, 0, 8, seed=0), list(mpo.site.qn))
+    for _ in range(4):
+        g = eng.sweep(24)
+    e0 = exact.tfim_energy(L, 1.0, h)
+    assert g["energy"] >= e0 - 1e-10
+    assert abs(g["energy"] - e0) < 1e-8 * abs(e0)
+
+
+def test_aklt_exact():
+    L = 20
+    mpo = wl.aklt_chain(L)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, wl.random_mps(L, mpo.site.qn, 0, 8, seed=0), list(mpo.site.qn))
+    for _ in range(4):
+        g = eng.sweep(8)
+    assert abs(g["energy"] - exact.aklt_energy(L)) < 1e-10
+
+
+def test_cylinder_against_ed():
+    mpo = wl.heisenberg_square_cylinder(4, 3)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, wl.random_mps(mpo.L, mpo.site.qn, 0, 64, seed=1), list(mpo.site.qn))
+    for _ in range(4):
+        g = eng.sweep(100)
+    assert abs(g["energy"] - GOLD["heisenberg_cylinder_4x3_Sz0"]) < 1e-9
+
+
+@pytest.mark.parametrize("R,warm", [(2, 1), (4, 0)])
+def test_regions_match_oracle(R, warm):
+    L = 16
+    mpo = wl.heisenberg_chain(L)
+    mps = wl.random_mps(L, mpo.site.qn, 0, 8, seed=0)
+    ref = P.ParallelDMRG(mpo, mps, R)
+    ref.setup(32, warmup_sweeps=warm)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, mps, list(mpo.site.qn))
+    eng.setup_regions(R, warm, 32)
+    for k in range(R):
+        assert eng.center(k) == ref.regions[k].oc
+    for sweep, m in enumerate((32, 64, 64)):
+        r = ref.sweep(m)
+        g = eng.sweep(m)
+        assert abs(g["energy"] - r["energy"]) <= TOL * abs(r["energy"]), sweep
+        fids = [x["fidelity"] for x in r["merges"]]
+        assert abs(g["max_fidelity"] - max(fids)) <= 1e-7
+    assert abs(g["energy"] - GOLD["heisenberg_chain_L16_Sz0"]) < 1e-7

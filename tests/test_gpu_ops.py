@@ -1,0 +1,124 @@
+"""GPU parity of single hot-path operations (C ABI, FP64 mode) against the CPU oracle:
+projected-Hamiltonian matvec, projected-operator updates, SVD split with truncation."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import dmrg as O
+from tests import _layout as LY
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+pd = pytest.importorskip("paper_1301_3494_gb300")
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _bond_case(kind, m, seed):
+    """Random bond sectors of total size ~m around a chain / cylinder MPO."""
+    rng = np.random.default_rng(seed)
+    if kind == "chain":
+        mpo = wl.heisenberg_chain(40)
+        j = 20
+    elif kind == "cyl":
+        mpo = wl.heisenberg_square_cylinder(6, 4)
+        j = 11
+    else:
+        mpo = wl.tfim_chain(30, 1.0, 0.7)
+        j = 15
+    qn = list(mpo.site.qn)
+    bonds = wl.bond_sectors(mpo.L, qn, 0, m, sigma=None if kind == "tfim" else 3.0)
+    return mpo, qn, bonds[j], bonds[j + 2], bonds[j + 1], j, rng
+
+
+@pytest.mark.parametrize("kind,m", [("chain", 40), ("chain", 300), ("cyl", 150), ("tfim", 150)])
+def test_heff_apply_fp64_matches_oracle(kind, m):
+    mpo, qn, bl, br, _, j, rng = _bond_case(kind, m, 1)
+    W1, W2 = mpo.W[j], mpo.W[j + 1]
+    f0, f1, f2 = mpo.flux[j], mpo.flux[j + 1], mpo.flux[j + 2]
+    Lenv = LY.random_env(bl, f0, rng)
+    Renv = LY.random_env(br, f2, rng)
+    psi = {k: rng.standard_normal((bl[k[0]], br[k[0] + qn[k[1]] + qn[k[2]]])) for k in LY.psi_keys(bl, br, qn)}
+    ref = O.heff_apply(Lenv, W1, f0, W2, f2, Renv, psi, qn)
+    bond = pd.Bond(qn, bl, br, W1, f0, f1, W2, f2)
+    Ld, Rd = _dev(LY.pack_env(Lenv, bl, f0)), _dev(LY.pack_env(Renv, br, f2))
+    x = _dev(LY.pack_psi(psi, bl, br, qn))
+    y = torch.zeros_like(x)
+    flops = pd.heff_apply(bond, pd.FP64, Ld.data_ptr(), Rd.data_ptr(), x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    got = LY.unpack_psi(y.cpu().numpy(), bl, br, qn)
+    scale = max(np.abs(v).max() for v in ref.values())
+    for k in ref:
+        assert np.abs(got[k] - ref[k]).max() <= 1e-12 * scale, k
+    assert flops > 0
+
+
+@pytest.mark.parametrize("kind,m", [("chain", 60), ("cyl", 200), ("tfim", 100)])
+def test_env_updates_fp64_match_oracle(kind, m):
+    mpo, qn, bl, _, bm, j, rng = _bond_case(kind, m, 2)
+    W = mpo.W[j]
+    fL, fR = mpo.flux[j], mpo.flux[j + 1]
+    A = {k: rng.standard_normal((bl[k[0]], bm[k[0] + qn[k[1]]])) for k in LY.site_keys(bl, bm, qn)}
+    Lin = LY.random_env(bl, fL, rng)
+    ref = O.env_left(Lin, A, W, fL, fR, qn)
+    bond = pd.Bond(qn, bl, bm, W, fL, fR)
+    Lo = torch.zeros(len(LY.env_keys(bm, fR)) and sum(bm[q] * bm[q - int(fR[w])] for q, w in LY.env_keys(bm, fR)),
+                     dtype=torch.float64, device="cuda")
+    pd.env_left(bond, pd.FP64, _dev(LY.pack_env(Lin, bl, fL)).data_ptr(), _dev(LY.pack_site(A, bl, bm, qn)).data_ptr(),
+                Lo.data_ptr())
+    torch.cuda.synchronize()
+    got = LY.unpack_env(Lo.cpu().numpy(), bm, fR)
+    scale = max(np.abs(v).max() for v in ref.values())
+    for k in LY.env_keys(bm, fR):
+        r = ref.get(k, np.zeros_like(got[k]))
+        assert np.abs(got[k] - r).max() <= 1e-12 * scale, k
+    # right update through the same site
+    Rin = LY.random_env(bm, fR, rng)
+    refR = O.env_right(Rin, A, W, fL, fR, qn)
+    Ro = torch.zeros(sum(bl[q] * bl[q - int(fL[w])] for q, w in LY.env_keys(bl, fL)), dtype=torch.float64, device="cuda")
+    pd.env_right(bond, pd.FP64, _dev(LY.pack_env(Rin, bm, fR)).data_ptr(), _dev(LY.pack_site(A, bl, bm, qn)).data_ptr(),
+                 Ro.data_ptr())
+    torch.cuda.synchronize()
+    gotR = LY.unpack_env(Ro.cpu().numpy(), bl, fL)
+    scale = max(np.abs(v).max() for v in refR.values())
+    for k in LY.env_keys(bl, fL):
+        r = refR.get(k, np.zeros_like(gotR[k]))
+        assert np.abs(gotR[k] - r).max() <= 1e-12 * scale, k
+
+
+@pytest.mark.parametrize("kind,m,mmax", [("chain", 60, 1000), ("chain", 200, 120), ("cyl", 160, 90), ("tfim", 80, 50)])
+def test_svd_split_matches_oracle(kind, m, mmax):
+    mpo, qn, bl, br, _, j, rng = _bond_case(kind, m, 3)
+    # a wavefunction with a decaying spectrum (like a ground state)
+    psi = {}
+    for k in LY.psi_keys(bl, br, qn):
+        a, c = bl[k[0]], br[k[0] + qn[k[1]] + qn[k[2]]]
+        psi[k] = rng.standard_normal((a, c)) * np.exp(-0.05 * np.add.outer(np.arange(a), np.arange(c)))
+    A, lam, B, counts, err = O.split_two_site(psi, bl, br, qn, mmax)
+    bond = pd.Bond(qn, bl, br, mpo.W[j], mpo.flux[j], mpo.flux[j + 1])
+    x = _dev(LY.pack_psi(psi, bl, br, qn))
+    n = x.numel()
+    Ad = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+    Bd = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+    ld = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+    mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, False, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
+    torch.cuda.synchronize()
+    assert mid == counts                                   # block table bit-exact
+    assert abs(tr - err) <= 1e-12 + 1e-9 * err
+    lam_ref = np.concatenate([lam[q] for q in sorted(lam)])
+    lam_gpu = ld.cpu().numpy()[: lam_ref.size]
+    assert np.abs(lam_gpu - lam_ref).max() <= 1e-12
+    # factors: orthonormal, and A diag(lam) B reproduces the oracle's truncated Psi
+    Ag = LY.unpack_site(Ad.cpu().numpy(), bl, mid, qn)
+    Bg = LY.unpack_site(Bd.cpu().numpy(), mid, br, qn)
+    lg, off = {}, 0
+    for q in sorted(mid):
+        lg[q] = lam_gpu[off: off + mid[q]]
+        off += mid[q]
+    rec_g = O.two_site({k: v * lg[k[0] + qn[k[1]]][None, :] for k, v in Ag.items()}, Bg, qn)
+    rec_o = O.two_site({k: v * lam[k[0] + qn[k[1]]][None, :] for k, v in A.items()}, B, qn)
+    for k in rec_o:
+        assert np.abs(rec_g[k] - rec_o[k]).max() <= 1e-11, k
