@@ -64,14 +64,29 @@ struct Chain {
         err.ensure(4, st);
         PD_CK(cudaMemsetAsync(err.p, 0, 4, st));
     }
-    ~Chain() {
-        if (own_stream && st) cudaStreamDestroy(st);
+    void rebind_all() {
+        for (auto& b : site) b.rebind(st);
+        for (auto& e : Lenv) if (e) e->rebind(st);
+        for (auto& e : Renv) if (e) e->rebind(st);
+        err.rebind(st);
+    }
+};
+
+// Streams created by the context; destroyed after every buffer that may free on them.
+struct StreamHolder {
+    std::vector<cudaStream_t> s;
+    ~StreamHolder() {
+        for (auto x : s) {
+            cudaStreamSynchronize(x);
+            cudaStreamDestroy(x);
+        }
     }
 };
 
 }  // namespace
 
 struct dmrg_ctx {
+    StreamHolder streams;                            // first member: destroyed last
     int L = 0, d = 0, qtot = 0;
     std::vector<int> qn;
     std::vector<SiteMPO> W;
@@ -391,17 +406,19 @@ void do_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fid_out, d
     check_err_word(left.err.as<unsigned>(), st);
     std::vector<double> V(sr.lam.size());
     for (size_t i = 0; i < V.size(); ++i) V[i] = 1.0 / sr.lam[i];
-    c->V[b] = V;
-    c->Vbond[b] = sr.mid;
+    c->V.at(b) = V;            // keys exist since set-up: lookups only, safe across region threads
+    c->Vbond.at(b) = sr.mid;
     left.bond[b] = sr.mid;
     right.bond[b] = sr.mid;
     left.lam[b] = sr.lam;
     right.lam[b] = sr.lam;
+    PD_CK(cudaStreamSynchronize(st));
+    psi4.rebind(right.st);
+    Lnew->rebind(right.st);
     left.site[b - 1] = std::move(psi3);
     right.site[b] = std::move(psi4);
     left.Renv[b] = std::move(Rnew);
     right.Lenv[b] = std::move(Lnew);
-    PD_CK(cudaStreamSynchronize(st));
     stream_after(right.st, st);
     if (fid_out) *fid_out = fid;
     if (e_out) *e_out = r.theta;
@@ -493,6 +510,7 @@ void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
         std::unique_ptr<Chain> r(new Chain());
         cudaStream_t rs;
         PD_CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+        c->streams.s.push_back(rs);
         r->init(L, rs);
         r->own_stream = true;
         r->p = bounds[k];
@@ -510,6 +528,7 @@ void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
         }
         for (int b = r->p + 1; b <= r->q + 1; ++b) r->Renv[b] = std::move(ch.Renv[b]);
         r->oc = r->p;
+        r->rebind_all();
         c->reg.push_back(std::move(r));
     }
     // staggered start (Fig. 4): even regions (1-based) move to their right end
@@ -759,11 +778,10 @@ dmrg_status dmrg_get_center(dmrg_ctx* c, int region, int* site) {
 
 dmrg_status dmrg_destroy(dmrg_ctx* c) {
     if (!c) return DMRG_OK;
-    cudaStream_t st = c->base;
-    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(c->base);
     for (auto& r : c->reg)
         if (r->st) cudaStreamSynchronize(r->st);
-    delete c;
+    delete c;   // buffers free on their streams, then the owned streams are destroyed
     return DMRG_OK;
 }
 

@@ -77,6 +77,8 @@ struct DBuf {
         st = s;
     }
     template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+    // Hand the buffer to another stream: later frees are ordered after that stream's work.
+    void rebind(cudaStream_t s) { st = s; }
 };
 
 template <class T>
@@ -209,6 +211,10 @@ struct EnvSlab {
     DBuf op;                  // bf16 operand copy (BF16 mode)
     bool op_valid = false;
     bool valid = false;
+    void rebind(cudaStream_t s) {
+        buf.rebind(s);
+        op.rebind(s);
+    }
 };
 
 // ------------------------------------------------------------------------------------------

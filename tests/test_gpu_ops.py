@@ -67,8 +67,8 @@ def test_env_updates_fp64_match_oracle(kind, m):
     bond = pd.Bond(qn, bl, bm, W, fL, fR)
     Lo = torch.zeros(len(LY.env_keys(bm, fR)) and sum(bm[q] * bm[q - int(fR[w])] for q, w in LY.env_keys(bm, fR)),
                      dtype=torch.float64, device="cuda")
-    pd.env_left(bond, pd.FP64, _dev(LY.pack_env(Lin, bl, fL)).data_ptr(), _dev(LY.pack_site(A, bl, bm, qn)).data_ptr(),
-                Lo.data_ptr())
+    Lin_d, A_d = _dev(LY.pack_env(Lin, bl, fL)), _dev(LY.pack_site(A, bl, bm, qn))   # keep references alive
+    pd.env_left(bond, pd.FP64, Lin_d.data_ptr(), A_d.data_ptr(), Lo.data_ptr())
     torch.cuda.synchronize()
     got = LY.unpack_env(Lo.cpu().numpy(), bm, fR)
     scale = max(np.abs(v).max() for v in ref.values())
@@ -79,8 +79,8 @@ def test_env_updates_fp64_match_oracle(kind, m):
     Rin = LY.random_env(bm, fR, rng)
     refR = O.env_right(Rin, A, W, fL, fR, qn)
     Ro = torch.zeros(sum(bl[q] * bl[q - int(fL[w])] for q, w in LY.env_keys(bl, fL)), dtype=torch.float64, device="cuda")
-    pd.env_right(bond, pd.FP64, _dev(LY.pack_env(Rin, bm, fR)).data_ptr(), _dev(LY.pack_site(A, bl, bm, qn)).data_ptr(),
-                 Ro.data_ptr())
+    Rin_d = _dev(LY.pack_env(Rin, bm, fR))
+    pd.env_right(bond, pd.FP64, Rin_d.data_ptr(), A_d.data_ptr(), Ro.data_ptr())
     torch.cuda.synchronize()
     gotR = LY.unpack_env(Ro.cpu().numpy(), bl, fL)
     scale = max(np.abs(v).max() for v in refR.values())
