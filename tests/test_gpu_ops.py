@@ -122,3 +122,64 @@ def test_svd_split_matches_oracle(kind, m, mmax):
     rec_o = O.two_site({k: v * lam[k[0] + qn[k[1]]][None, :] for k, v in A.items()}, B, qn)
     for k in rec_o:
         assert np.abs(rec_g[k] - rec_o[k]).max() <= 1e-11, k
+
+
+# ------------------------------------------------------------------------------------------
+# Tensor-core (tcgen05) paths: normwise relative error against the FP64 oracle.  Bounds from
+# the operand rounding: bf16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3; psi, L, R and
+# the MPO-mixed intermediate are rounded once each), tf32 keeps 11 (2^-11 ~ 5e-4, truncation).
+# ------------------------------------------------------------------------------------------
+TC_TOL = {pd.BF16: 2e-2, pd.TF32: 5e-3}
+
+
+def _nrel(got, ref):
+    a = np.concatenate([got[k].ravel() for k in ref])
+    b = np.concatenate([ref[k].ravel() for k in ref])
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [pd.BF16, pd.TF32])
+@pytest.mark.parametrize("kind,m", [("chain", 40), ("chain", 700), ("cyl", 1000), ("tfim", 300)])
+def test_heff_apply_tensor_core(prec, kind, m):
+    mpo, qn, bl, br, _, j, rng = _bond_case(kind, m, 4)
+    W1, W2 = mpo.W[j], mpo.W[j + 1]
+    f0, f1, f2 = mpo.flux[j], mpo.flux[j + 1], mpo.flux[j + 2]
+    Lenv = LY.random_env(bl, f0, rng)
+    Renv = LY.random_env(br, f2, rng)
+    psi = {k: rng.standard_normal((bl[k[0]], br[k[0] + qn[k[1]] + qn[k[2]]])) for k in LY.psi_keys(bl, br, qn)}
+    ref = O.heff_apply(Lenv, W1, f0, W2, f2, Renv, psi, qn)
+    bond = pd.Bond(qn, bl, br, W1, f0, f1, W2, f2)
+    Ld, Rd = _dev(LY.pack_env(Lenv, bl, f0)), _dev(LY.pack_env(Renv, br, f2))
+    x = _dev(LY.pack_psi(psi, bl, br, qn))
+    y = torch.zeros_like(x)
+    pd.heff_apply(bond, prec, Ld.data_ptr(), Rd.data_ptr(), x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    got = LY.unpack_psi(y.cpu().numpy(), bl, br, qn)
+    err = _nrel(got, ref)
+    assert err <= TC_TOL[prec], err
+    assert err > 0.0        # the tensor-core path really ran in reduced precision
+
+
+@pytest.mark.parametrize("kind,m", [("chain", 500), ("cyl", 800)])
+def test_env_updates_tf32(kind, m):
+    mpo, qn, bl, _, bm, j, rng = _bond_case(kind, m, 5)
+    W = mpo.W[j]
+    fL, fR = mpo.flux[j], mpo.flux[j + 1]
+    A = {k: rng.standard_normal((bl[k[0]], bm[k[0] + qn[k[1]]])) for k in LY.site_keys(bl, bm, qn)}
+    Lin = LY.random_env(bl, fL, rng)
+    Rin = LY.random_env(bm, fR, rng)
+    bond = pd.Bond(qn, bl, bm, W, fL, fR)
+    Lin_d, A_d, Rin_d = _dev(LY.pack_env(Lin, bl, fL)), _dev(LY.pack_site(A, bl, bm, qn)), _dev(LY.pack_env(Rin, bm, fR))
+    Lo = torch.zeros(sum(bm[q] * bm[q - int(fR[w])] for q, w in LY.env_keys(bm, fR)), dtype=torch.float64, device="cuda")
+    Ro = torch.zeros(sum(bl[q] * bl[q - int(fL[w])] for q, w in LY.env_keys(bl, fL)), dtype=torch.float64, device="cuda")
+    pd.env_left(bond, pd.TF32, Lin_d.data_ptr(), A_d.data_ptr(), Lo.data_ptr())
+    pd.env_right(bond, pd.TF32, Rin_d.data_ptr(), A_d.data_ptr(), Ro.data_ptr())
+    torch.cuda.synchronize()
+    refL = O.env_left(Lin, A, W, fL, fR, qn)
+    refR = O.env_right(Rin, A, W, fL, fR, qn)
+    gotL = LY.unpack_env(Lo.cpu().numpy(), bm, fR)
+    gotR = LY.unpack_env(Ro.cpu().numpy(), bl, fL)
+    refL = {k: refL.get(k, np.zeros_like(gotL[k])) for k in gotL}
+    refR = {k: refR.get(k, np.zeros_like(gotR[k])) for k in gotR}
+    assert _nrel(gotL, refL) <= 5e-3
+    assert _nrel(gotR, refR) <= 5e-3
