@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark: H_eff matvec TFLOP/s and sweep seconds of two-site DMRG on the spin-1/2
+Heisenberg 24x8 square cylinder (periodic width 8, open length 24, snake order, MPO bond
+dimension 26) at m = 2000, mixed precision (bf16 tensor-core matvec, FP64 Davidson/SVD).
+
+A step is one two-site bond update in the bulk of the cylinder (form Psi, Davidson with a
+fixed number of iterations, SVD + truncation to m, environment update), run through the
+library's public C ABI (dmrg_advance).  Inputs are synthetic: a seeded random
+mixed-canonical MPS whose U(1) sector dimensions follow a Gaussian profile (sigma = 5 in
+2S^z units, ~17 sectors, largest ~320) -- the shape of a ground state's Schmidt spectrum.
+
+Prints one JSON line.  --impl reference times the CPU oracle on the host cores instead.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "H_eff matvec TFLOP/s & sweep s, 24x8 m=2000; mixed vs FP64 GPU at 1e-5 dE/E"
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (per GPU)
+FP64_PEAK_TFLOPS = 1.25                 # nominal FP64 rate of a GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16", "tf32", "fp64"], default="bf16")
+    ap.add_argument("--lx", type=int, default=24)
+    ap.add_argument("--ly", type=int, default=8)
+    ap.add_argument("--m", type=int, default=2000)
+    ap.add_argument("--sigma", type=float, default=5.0)
+    ap.add_argument("--dav-iters", type=int, default=4)
+    ap.add_argument("--kmax", type=int, default=8)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-sample-s", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# Workload
+# ------------------------------------------------------------------------------------------
+def workload(args):
+    mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
+    qn = list(mpo.site.qn)
+    L = mpo.L
+    center = L // 2 - (args.warmup + args.steps) // 2
+    mps = wl.isometric_mps(L, qn, 0, args.m, args.seed, center, sigma=args.sigma)
+    return mpo, qn, mps, center
+
+
+def heff_flops(bl, br, qn, W1, f0, W2, f2):
+    """Algorithmic flops of one projected-Hamiltonian application with nonzero blocks and
+    nonzero MPO channels only: L stage (2 m_c m_a' m_a per kept block pair), MPO mixing
+    (2 flops per element per term), R stage (2 m_c' m_a' m_c per segment).  Counting only."""
+    d = len(qn)
+    W12 = np.einsum("aijb,bklc->aijklc", W1, W2)
+    nz = np.argwhere(W12 != 0)
+    used = {(int(w), int(s1p), int(s2p)) for w, _, s1p, _, s2p, _ in nz}
+    blocks = [(qa, s1, s2) for qa in bl for s1 in range(d) for s2 in range(d) if qa + qn[s1] + qn[s2] in br]
+    fl = 0.0
+    X = {}
+    for (qa, s1p, s2p) in blocks:
+        qc = qa + qn[s1p] + qn[s2p]
+        for w in range(W1.shape[0]):
+            qab = qa + int(f0[w])
+            if (w, s1p, s2p) in used and qab in bl:
+                X[(w, qa, s1p, s2p)] = (qab, qc)
+                fl += 2.0 * br[qc] * bl[qab] * bl[qa]
+    groups = {}
+    for w, s1, s1p, s2, s2p, w2 in nz:
+        for (qa, a1, a2) in blocks:
+            if a1 != s1p or a2 != s2p or (w, qa, a1, a2) not in X:
+                continue
+            qab, qc = X[(w, qa, a1, a2)]
+            qcb = qab + qn[s1] + qn[s2]
+            if qcb not in br or (qcb - int(f2[w2])) not in br:
+                continue
+            g = groups.setdefault((qab, int(s1), int(s2), int(w2)), [0, qab, qc])
+            g[0] += 1
+    for (qab, s1, s2, w2), (nt, _, qc) in groups.items():
+        qcb = qab + qn[s1] + qn[s2]
+        fl += 2.0 * bl[qab] * br[qc] * nt + 2.0 * br[qcb] * bl[qab] * br[qc]
+    return fl
+
+
+# ------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for i, nm in enumerate(names):
+                if "Active" in r[5 + i] and "Not" not in r[5 + i]:
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def ncu_traffic(precision):
+    """Per-launch DRAM bytes of the matvec GEMM from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", f"tc_gemm_matvec_{precision}_traffic.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline field)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(mpo, qn, mps, j, seed=1):
+    """Random environments with the exact block structure of bond j of the benchmark state."""
+    from oracle import dmrg as O  # noqa: F401  (test-infrastructure import, CPU baseline only)
+    rng = np.random.default_rng(seed)
+    bl, br = mps.bonds[j], mps.bonds[j + 2]
+    f0, f2 = mpo.flux[j], mpo.flux[j + 2]
+
+    def env(bond, flux):
+        return {(q, w): rng.standard_normal((bond[q], bond[q - int(flux[w])]))
+                for q in bond for w in range(len(flux)) if (q - int(flux[w])) in bond}
+
+    Lenv, Renv = env(bl, f0), env(br, f2)
+    psi = {(qa, s1, s2): rng.standard_normal((bl[qa], br[qa + qn[s1] + qn[s2]]))
+           for qa in bl for s1 in range(len(qn)) for s2 in range(len(qn)) if qa + qn[s1] + qn[s2] in br}
+    fl = heff_flops(bl, br, qn, mpo.W[j], f0, mpo.W[j + 1], f2)
+    return (Lenv, mpo.W[j], f0, mpo.W[j + 1], f2, Renv, psi, qn), fl
+
+
+def time_oracle(sample, budget_s, min_reps=1):
+    from oracle import dmrg as O
+    args, fl = sample
+    reps, t_tot = 0, 0.0
+    while reps < min_reps or t_tot < budget_s:
+        t0 = time.perf_counter()
+        O.heff_apply(*args)
+        t_tot += time.perf_counter() - t0
+        reps += 1
+    return fl * reps / t_tot / 1e12, reps, t_tot
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ------------------------------------------------------------------------------------------
+# Distributed helpers (independent replicas, one per GPU)
+# ------------------------------------------------------------------------------------------
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        return rank, world, dist
+    return rank, world, None
+
+
+def main():
+    args = parse()
+    rank, world, dist = dist_init(args)
+    mpo, qn, mps, center = workload(args)
+    L = mpo.L
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sample = oracle_sample(mpo, qn, mps, center)
+        for _ in range(args.warmup):
+            time_oracle(sample, 0.0)
+        vals, t_all = [], 0.0
+        for _ in range(args.steps):
+            v, reps, t = time_oracle(sample, 0.0)
+            vals.append(v)
+            t_all += t
+        value = sum(vals) / len(vals)
+        cores = blas_threads()
+        out = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}",
+                       "D": max(mpo.D), "m": args.m, "bond": center, "precision": "fp64-oracle"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one full H_eff matvec of the CPU oracle per step at bond {center} "
+                                       f"of the {args.lx}x{args.ly} m={args.m} state (random environments "
+                                       "with that bond's block structure)"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(out))
+        return
+
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_1301_3494_gb300 as pd
+    if not os.path.exists(pd.LIB_PATH):
+        from paper_1301_3494_gb300 import build
+        build.build()
+    W, flux, D = wl.pack_mpo(mpo)
+    eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
+    data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
+    t_setup = time.perf_counter()
+    eng.set_mps(mps.bonds, data, center=center)
+    t_setup = time.perf_counter() - t_setup
+    dav = dict(dav_tol=0.0, dav_max_iter=args.dav_iters)     # a fixed number of Davidson steps
+    for _ in range(args.warmup):
+        eng.advance(1, args.m, **dav)
+    torch.cuda.synchronize()
+    pd.profile_reset()
+    pd.profile_enable(True)
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    w0 = time.perf_counter()
+    ev0.record()
+    for _ in range(args.steps):
+        stats.append(eng.advance(1, args.m, **dav))    # host params in, host stats out per step
+    ev1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clocks = clk.stop()
+    pd.profile_enable(False)
+    prof = pd.profile_read()
+    dev_s = ev0.elapsed_time(ev1) * 1e-3
+    if dist:
+        t = torch.tensor([dev_s, wall], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s, wall = float(t[0]), float(t[1])
+    mv_flops = sum(s["matvec_flops"] for s in stats)
+    mv_s = sum(s["matvec_seconds"] for s in stats)
+    value = world * mv_flops / mv_s / 1e12
+    ms_step = 1e3 * dev_s / args.steps
+    # roofline of the dominant kernel: the tensor-core GEMM of the matvec stages
+    pk, pk_kind = peaks()
+    if args.precision == "fp64":
+        g_ms, g_fl, g_n = prof["f64_gemm_ms"], prof["f64_gemm_flops"], prof["f64_gemm_launches"]
+        peak, bound = FP64_PEAK_TFLOPS, "alu"
+        peak_note = "nominal FP64 rate of a GB300 (1.25 TFLOP/s)"
+    else:
+        g_ms, g_fl, g_n = prof["mv_gemm_ms"], prof["mv_gemm_flops"], prof["mv_gemm_launches"]
+        peak = pk["bf16_tflops_sustained"] * (1.0 if args.precision == "bf16" else NOMINAL_TF32_OVER_BF16)
+        bound = "tensor"
+        peak_note = (f"{pk_kind} bf16 sustained" + ("" if args.precision == "bf16" else " x nominal tf32/bf16"))
+    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    tr = ncu_traffic(args.precision)
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": tr["bytes_per_launch"] if tr else None, "kernel": "k_tc_gemm (matvec L and R stages)",
+            "launches": g_n, "flops_per_launch": g_fl / max(g_n, 1), "peak_source": peak_note}
+    e2e_value = world * mv_flops / wall / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}", "D": max(mpo.D),
+                   "m": args.m, "sectors_at_bond": len(mps.bonds[center + 1]), "bond_start": center,
+                   "dav_iters": args.dav_iters, "kmax": args.kmax, "precision": args.precision,
+                   "regions": 1, "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
+                   "setup_s": t_setup},
+        "sweep_s": ms_step * 2 * (L - 1) / 1e3,
+        "sweep_s_note": "bulk step time at m=2000 x 2(L-1) steps",
+        "matvecs": sum(s["n_matvec"] for s in stats),
+        "matvec_ms": 1e3 * mv_s / max(1, sum(s["n_matvec"] for s in stats)),
+        "energy_last_step": stats[-1]["energy"],
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": ctypes.sizeof(pd.SweepParams),
+                "d2h_bytes_per_step": ctypes.sizeof(pd.SweepStats)},
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = oracle_sample(mpo, qn, mps, center)
+        v, reps, t = time_oracle(sample, args.cpu_sample_s)
+        out["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": blas_threads(), "kind": "oracle",
+                               "sample": f"{reps} H_eff matvecs of the CPU oracle ({t:.1f} s) at bond {center} "
+                                         "with random environments of that bond's block structure"}
+    if rank == 0:
+        print(json.dumps(out))
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -85,6 +85,10 @@ typedef struct {
     const int* sector_q;    /* concatenated sector charges, bond 0 first                      */
     const int* sector_m;    /* concatenated sector dimensions                                 */
     const double* data;     /* concatenated packed site tensors, site 0 first                 */
+    int canonical;          /* 0: arbitrary MPS, canonicalised by the engine (centre on site 0);
+                               1: already mixed-canonical -- sites < center left-orthonormal,
+                               sites > center right-orthonormal, normalised; no SVDs are run   */
+    int center;             /* orthogonality centre when canonical = 1                        */
 } dmrg_mps_desc;
 
 typedef struct {
@@ -126,10 +130,17 @@ typedef struct dmrg_ctx dmrg_ctx;
  * W entry that violates the flux rule. */
 dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_config* cfg);
 
-/* Load a matrix product state (packed layout above, host memory, copied), bring it to
- * right-canonical form with the orthogonality centre on site 0 by untruncated SVDs from the
- * right, normalise it, and build every right environment.  Serial mode afterwards. */
+/* Load a matrix product state (packed layout above, host memory, copied).  With canonical = 0
+ * the engine brings it to right-canonical form with the orthogonality centre on site 0 by
+ * untruncated SVDs from the right and normalises it; with canonical = 1 it trusts the given
+ * mixed-canonical gauge.  Then every environment on both sides of the centre is built.
+ * Serial mode afterwards. */
 dmrg_status dmrg_set_mps(dmrg_ctx* ctx, const dmrg_mps_desc* mps);
+
+/* Serial mode: n two-site steps continuing the current sweep (moving right until the centre
+ * reaches site L-1, then left until site 0, and so on).  2(L-1) steps from site 0 are one
+ * sweep.  Blocks until done; stats (nullable) cover these steps. */
+dmrg_status dmrg_advance(dmrg_ctx* ctx, int n_steps, const dmrg_sweep_params* p, dmrg_sweep_stats* stats);
 
 /* Real-space parallel set-up (Sec. II, Fig. 4): split the chain into n_regions blocks at
  * bonds round(k L / n_regions); run `warmup` serial sweeps (the last one's left half-sweep
@@ -172,6 +183,29 @@ dmrg_status dmrg_destroy(dmrg_ctx* ctx);
 /* Message of the last failure on this context (context-owned, valid until the next call). */
 const char* dmrg_last_error(const dmrg_ctx* ctx);
 const char* dmrg_status_string(int status);
+
+/* ------------------------------------------------------------------------------------------
+ * Instrumentation (process-wide).  Kernel launches are always counted; with profiling on, the
+ * grouped-GEMM launches are bracketed by CUDA events on their own stream and their device
+ * time and algorithmic flops are accumulated per class.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    long long launches;          /* kernels launched by the library since the last reset       */
+    long long mv_gemm_launches;  /* tensor-core GEMM launches of H_eff matvecs                  */
+    double mv_gemm_ms;           /* their summed device time                                    */
+    double mv_gemm_flops;        /* their algorithmic flops                                     */
+    long long env_gemm_launches; /* tensor-core GEMM launches of environment updates            */
+    double env_gemm_ms;
+    double env_gemm_flops;
+    long long f64_gemm_launches; /* FP64 grouped-GEMM launches (any use)                        */
+    double f64_gemm_ms;
+    double f64_gemm_flops;
+} dmrg_profile;
+
+void dmrg_profile_enable(int on);
+void dmrg_profile_reset(void);
+/* Synchronises the device, then copies the counters. */
+dmrg_status dmrg_profile_read(dmrg_profile* out);
 
 /* ------------------------------------------------------------------------------------------
  * Operation API: single steps on caller-provided device buffers (used for element-wise

@@ -30,7 +30,18 @@ class MpoDesc(C.Structure):
 
 
 class MpsDesc(C.Structure):
-    _fields_ = [("n_sectors", _ip), ("sector_q", _ip), ("sector_m", _ip), ("data", _dp)]
+    _fields_ = [("n_sectors", _ip), ("sector_q", _ip), ("sector_m", _ip), ("data", _dp),
+                ("canonical", C.c_int), ("center", C.c_int)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("mv_gemm_launches", C.c_longlong), ("mv_gemm_ms", C.c_double),
+                ("mv_gemm_flops", C.c_double), ("env_gemm_launches", C.c_longlong), ("env_gemm_ms", C.c_double),
+                ("env_gemm_flops", C.c_double), ("f64_gemm_launches", C.c_longlong), ("f64_gemm_ms", C.c_double),
+                ("f64_gemm_flops", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Config(C.Structure):
@@ -85,6 +96,12 @@ def lib():
         L.dmrg_set_mps.argtypes = [vp, C.POINTER(MpsDesc)]
         L.dmrg_setup_regions.argtypes = [vp, C.c_int, C.c_int, C.POINTER(SweepParams)]
         L.dmrg_sweep.argtypes = [vp, C.POINTER(SweepParams), C.POINTER(SweepStats)]
+        L.dmrg_advance.argtypes = [vp, C.c_int, C.POINTER(SweepParams), C.POINTER(SweepStats)]
+        L.dmrg_profile_enable.argtypes = [C.c_int]
+        L.dmrg_profile_enable.restype = None
+        L.dmrg_profile_reset.argtypes = []
+        L.dmrg_profile_reset.restype = None
+        L.dmrg_profile_read.argtypes = [C.POINTER(Profile)]
         L.dmrg_merge.argtypes = [vp, C.c_int, C.POINTER(SweepParams), _dp, _dp]
         L.dmrg_energy.argtypes = [vp, _dp]
         L.dmrg_get_bond.argtypes = [vp, C.c_int, _ip, _ip, C.c_int, _ip]
@@ -96,12 +113,27 @@ def lib():
         L.dmrg_env_right.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
         L.dmrg_svd_split.argtypes = [C.POINTER(BondDesc), vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, _ip, _ip, _ip,
                                      _dp, vp]
-        for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_merge",
+        for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
+                     "dmrg_profile_read", "dmrg_merge",
                      "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_destroy",
                      "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_svd_split"):
             getattr(L, name).restype = st
         _lib = L
     return _lib
+
+
+def profile_enable(on=True):
+    lib().dmrg_profile_enable(int(bool(on)))
+
+
+def profile_reset():
+    lib().dmrg_profile_reset()
+
+
+def profile_read():
+    p = Profile()
+    _check(lib().dmrg_profile_read(C.byref(p)))
+    return p.as_dict()
 
 
 def status_string(s):
@@ -196,13 +228,16 @@ class Engine:
     def params(m_max, dav_tol=1e-10, dav_max_iter=100):
         return SweepParams(int(m_max), float(dav_tol), int(dav_max_iter))
 
-    def set_mps(self, bonds, site_data):
-        """bonds: list of L+1 dicts charge -> dim; site_data: concatenated packed site tensors."""
+    def set_mps(self, bonds, site_data, center=None):
+        """bonds: list of L+1 dicts charge -> dim; site_data: concatenated packed site tensors.
+        center=None: the engine canonicalises; center=c: the tensors are already mixed-canonical
+        around site c."""
         ns = _i32([len(b) for b in bonds])
         sq = _i32([q for b in bonds for q in b.keys()])
         sm = _i32([m for b in bonds for m in b.values()])
         data = _f64(site_data)
-        desc = MpsDesc(_ptr(ns, _ip), _ptr(sq, _ip), _ptr(sm, _ip), _ptr(data, _dp))
+        desc = MpsDesc(_ptr(ns, _ip), _ptr(sq, _ip), _ptr(sm, _ip), _ptr(data, _dp),
+                       0 if center is None else 1, 0 if center is None else int(center))
         _check(lib().dmrg_set_mps(self._h, C.byref(desc)), self._h)
 
     def setup_regions(self, n_regions, warmup, m_max, dav_tol=1e-10, dav_max_iter=100):
@@ -213,6 +248,12 @@ class Engine:
         p = self.params(m_max, dav_tol, dav_max_iter)
         s = SweepStats()
         _check(lib().dmrg_sweep(self._h, C.byref(p), C.byref(s)), self._h)
+        return s.as_dict()
+
+    def advance(self, n_steps, m_max, dav_tol=1e-10, dav_max_iter=100):
+        p = self.params(m_max, dav_tol, dav_max_iter)
+        s = SweepStats()
+        _check(lib().dmrg_advance(self._h, int(n_steps), C.byref(p), C.byref(s)), self._h)
         return s.as_dict()
 
     def merge(self, k, m_max, dav_tol=1e-10, dav_max_iter=100):

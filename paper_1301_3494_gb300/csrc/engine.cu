@@ -99,6 +99,7 @@ struct dmrg_ctx {
     std::map<int, std::vector<double>> V;   // boundary bond -> V = 1/lambda (sector order of that bond)
     std::map<int, Sec> Vbond;
     bool have_state = false;
+    int dir = 1;                                     // serial sweep direction of dmrg_advance
     std::string last_err;
 
     const TwoSiteMPO& pair(int j) {
@@ -654,10 +655,23 @@ dmrg_status dmrg_set_mps(dmrg_ctx* c, const dmrg_mps_desc* m) {
         off += S.size;
     }
     PD_CK(cudaStreamSynchronize(ch.st));
-    right_canonicalize(c, ch);
+    int center = 0;
+    if (m->canonical) {
+        PD_REQUIRE(m->center >= 0 && m->center < c->L, DMRG_ERR_ARG, "centre outside the chain");
+        center = m->center;
+        ch.oc = center;
+    } else {
+        right_canonicalize(c, ch);
+    }
     make_boundary_envs(c, ch);
-    build_right_envs(c, ch, 2);
+    build_right_envs(c, ch, center + 1);
+    for (int j = 0; j < center; ++j) {
+        env_alloc(*ch.Lenv[j + 1], ch.bond[j + 1], c->W[j].fr, c->prec, ch.st);
+        env_update_left(ch.bond[j], ch.bond[j + 1], c->qn, c->W[j], *ch.Lenv[j], ch.site[j].as<double>(),
+                        *ch.Lenv[j + 1], c->prec, ch.err.as<unsigned>(), ch.st);
+    }
     check_err_word(ch.err.as<unsigned>(), ch.st);
+    c->dir = center < c->L - 1 ? 1 : -1;
     c->have_state = true;
     return DMRG_OK;
     CTX_CATCH(c)
@@ -695,6 +709,40 @@ dmrg_status dmrg_sweep(dmrg_ctx* c, const dmrg_sweep_params* p, dmrg_sweep_stats
         stats->matvec_flops = tot.mv_flops;
         stats->min_fidelity = tot.fid_min;
         stats->max_fidelity = tot.fid_max;
+    }
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_advance(dmrg_ctx* c, int n_steps, const dmrg_sweep_params* p, dmrg_sweep_stats* stats) {
+    CTX_TRY
+    PD_REQUIRE(c && p && n_steps >= 0, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->have_state && c->reg.empty(), DMRG_ERR_STATE, "advance needs a serial state");
+    PD_REQUIRE(p->m_max >= 1 && p->dav_max_iter >= 1 && p->dav_tol >= 0, DMRG_ERR_ARG, "bad sweep parameters");
+    auto t0 = std::chrono::steady_clock::now();
+    Chain& ch = *c->serial;
+    ch.acc = StepStats();
+    for (int i = 0; i < n_steps; ++i) {
+        if (c->dir > 0 && ch.oc >= c->L - 1) c->dir = -1;
+        if (c->dir < 0 && ch.oc <= 0) c->dir = 1;
+        if (c->dir > 0) bond_step(c, ch, ch.oc, true, p);
+        else bond_step(c, ch, ch.oc - 1, false, p);
+    }
+    check_err_word(ch.err.as<unsigned>(), ch.st);
+    auto t1 = std::chrono::steady_clock::now();
+    if (stats) {
+        const StepStats& tot = ch.acc;
+        stats->energy = tot.energy;
+        stats->max_trunc_err = tot.trunc;
+        stats->max_m = tot.m;
+        stats->n_matvec = tot.matvecs;
+        stats->n_steps = tot.steps;
+        stats->dav_nonconv = tot.nonconv;
+        stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+        stats->matvec_seconds = tot.mv_ms * 1e-3;
+        stats->matvec_flops = tot.mv_flops;
+        stats->min_fidelity = -1.0;
+        stats->max_fidelity = -1.0;
     }
     return DMRG_OK;
     CTX_CATCH(c)

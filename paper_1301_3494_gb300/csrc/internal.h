@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -30,6 +31,24 @@ struct Error {
     do {                                                                                  \
         if (!(cond)) throw ::pd::Error{code, what};                                       \
     } while (0)
+
+// Kernel launches issued by the library (process-wide counter).
+extern std::atomic<long long> g_launches;
+#define PD_LAUNCHED()                                                   \
+    do {                                                                \
+        PD_CK(cudaGetLastError());                                      \
+        ::pd::g_launches.fetch_add(1, std::memory_order_relaxed);       \
+    } while (0)
+
+// Profiling classes of grouped-GEMM launches; the class of tensor-core launches comes from the
+// calling thread's current activity.
+enum ProfClass { PROF_MV = 0, PROF_ENV = 1, PROF_F64 = 2 };
+extern thread_local int g_prof_class;
+bool prof_on();
+// With profiling on: record an event pair around a launch (call prof_start before the launch,
+// prof_stop after); the elapsed time is resolved in dmrg_profile_read.
+void* prof_start(cudaStream_t st);
+void prof_stop(void* token, cudaStream_t st, int cls, double flops);
 
 // Device error word bits (written by kernels, read by the host after a step).
 enum : unsigned {

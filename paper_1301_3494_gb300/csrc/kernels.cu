@@ -483,7 +483,7 @@ void launch_gemm64(const GProb* probs, const GSeg* segs, const GTile* tiles, int
                    const double* A, const double* B, double* C, cudaStream_t st) {
     if (ntiles <= 0) return;
     k_gemm64<<<ntiles, 256, 0, st>>>(probs, segs, tiles, A, B, C);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 template <class Tin, class Tout>
@@ -492,7 +492,7 @@ void launch_copy(const CopyJob* jobs, int njobs, int max_elems, const Tin* src, 
     PD_REQUIRE(njobs <= 65535, DMRG_ERR_CAPACITY, "too many copy jobs in one launch");
     dim3 g(grid_for(max_elems, 512), njobs);
     k_copy<Tin, Tout><<<g, 256, 0, st>>>(jobs, src, dst);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 template <class Tin, class Tout>
@@ -502,7 +502,7 @@ void launch_mix(const MixJob* jobs, int njobs, int max_elems, const MixTerm* ter
     PD_REQUIRE(njobs <= 65535, DMRG_ERR_CAPACITY, "too many mix jobs in one launch");
     dim3 g(grid_for(max_elems, 512), njobs);
     k_mix<Tin, Tout><<<g, 256, 0, st>>>(jobs, terms, in, out);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 template <class T>
@@ -512,7 +512,7 @@ void launch_diag(const DiagJob* jobs, int njobs, int max_elems, const DiagTerm* 
     PD_REQUIRE(njobs <= 65535, DMRG_ERR_CAPACITY, "too many diagonal jobs in one launch");
     dim3 g(grid_for(max_elems, 512), njobs);
     k_diag<T><<<g, 256, 0, st>>>(jobs, terms, Ls, ldl, Rs, ldr, out);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 template void launch_copy<double, double>(const CopyJob*, int, int, const double*, double*, cudaStream_t);
@@ -531,40 +531,40 @@ void launch_dots(const double* V, long long ldv, int k, const double* y, long lo
                  int nchunks, double* out, cudaStream_t st) {
     if (k <= 0) return;
     k_dots_partial<<<dim3(nchunks, k), 256, 0, st>>>(V, ldv, y, n, partial);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
     k_reduce_rows<<<k, 256, 0, st>>>(partial, nchunks, out);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_ritz(const double* V, const double* AV, long long ldv, int k, const double* yth, long long n,
                  double* u, double* Au, double* r, double* partial, int nchunks, double* norms, cudaStream_t st) {
     k_ritz<<<nchunks, 256, 0, st>>>(V, AV, ldv, k, yth, n, u, Au, r, partial);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
     k_reduce_rows<<<2, 256, 0, st>>>(partial, nchunks, norms);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_precond(const double* r, const double* diag, const double* theta, double fl, long long n,
                     double* t, cudaStream_t st) {
     k_precond<<<grid_for(n), 256, 0, st>>>(r, diag, theta, fl, n, t);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_subtract(const double* V, long long ldv, int k, const double* c, long long n, double* t,
                      cudaStream_t st) {
     k_subtract<<<grid_for(n), 256, 0, st>>>(V, ldv, k, c, n, t);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_scale(const double* x, const double* nrm2, long long n, double* y, int invert_sqrt, cudaStream_t st) {
     k_scale<<<grid_for(n), 256, 0, st>>>(x, nrm2, n, y, invert_sqrt);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_small_eig(const double* G, int k, int ldg, double* yth, cudaStream_t st) {
     PD_REQUIRE(k >= 1 && k <= 32, DMRG_ERR_CAPACITY, "Davidson subspace larger than 32");
     k_small_eig<<<1, 32, 0, st>>>(G, k, ldg, yth);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_nrm2(const double* x, long long n, double* partial, int nchunks, double* out, cudaStream_t st) {
@@ -573,13 +573,13 @@ void launch_nrm2(const double* x, long long n, double* partial, int nchunks, dou
 
 void launch_finite_check(const double* x, long long n, unsigned* err, cudaStream_t st) {
     k_finite<<<grid_for(n, 1024), 256, 0, st>>>(x, n, err);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, double* V, cudaStream_t st) {
     if (nsec <= 0) return;
     k_svd_init_v<<<dim3(grid_for((long long)max_n * max_n, 256), nsec), 256, 0, st>>>(secs, V);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_jacobi_round(const SvdSec* secs, const int* pair_sec, int npairs, int round, double* W, double* V,
@@ -588,7 +588,7 @@ void launch_jacobi_round(const SvdSec* secs, const int* pair_sec, int npairs, in
     int warps_per_block = 8;
     int blocks = (npairs + warps_per_block - 1) / warps_per_block;
     k_jacobi_round<<<blocks, 32 * warps_per_block, 0, st>>>(secs, pair_sec, npairs, round, W, V, tol, rotated);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_svd_finish(const SvdSec* secs, int nsec, int max_n, const double* W, double* sig, int* order,
@@ -596,7 +596,7 @@ void launch_svd_finish(const SvdSec* secs, int nsec, int max_n, const double* W,
     if (nsec <= 0) return;
     (void)max_n;
     k_svd_finish<<<nsec, 256, 0, st>>>(secs, W, sig, order);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 void launch_truncate(const SvdSec* secs, int nsec, const double* sig, const int* order, int total, int m_max,
@@ -607,7 +607,7 @@ void launch_truncate(const SvdSec* secs, int nsec, const double* sig, const int*
     if (smem > 48 * 1024)
         PD_CK(cudaFuncSetAttribute(k_truncate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_truncate<<<1, 1024, smem, st>>>(secs, nsec, sig, order, total, m_max, rel_cutoff, degen_tol, kept, weights);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 }  // namespace pd

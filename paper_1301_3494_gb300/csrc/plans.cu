@@ -127,7 +127,9 @@ void GemmBatch::upload_tiles(int tm, int tn, cudaStream_t st) {
 void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st) {
     if (g.empty()) return;
     g.upload_tiles(64, 64, st);
+    void* tok = prof_on() ? prof_start(st) : nullptr;
     launch_gemm64(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);
+    if (tok) prof_stop(tok, st, PROF_F64, g.flops);
 }
 
 template <class Tin>
@@ -263,14 +265,14 @@ void scale_site(const Sec& bl, const Sec& br, const std::vector<int>& qn, const 
     DBuf dj;
     upload(dj, jobs, st);
     k_rcscale<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<RCJob>(), in, lam, out);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
     PD_CK(cudaStreamSynchronize(st));
 }
 
 void scale_vec(double* x, long long n, double s, cudaStream_t st) {
     if (n <= 0) return;
     k_scale_plain<<<gridn(n), 256, 0, st>>>(x, n, s);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
 }
 
 double dot_host(const double* x, const double* y, long long n, cudaStream_t st) {
@@ -428,6 +430,7 @@ static const void* env_operand(const EnvSlab& e, int prec) {
 
 void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x, double* y,
                 unsigned* err, cudaStream_t st) {
+    g_prof_class = PROF_MV;
     const int prec = P.prec;
     const Num t = mv_num(prec);
     run_copy<double>(P.pack, x, P.psiT.p, t, st);
@@ -540,6 +543,7 @@ static void run_env_gemm(GemmBatch& g, int prec, const void* A, long long arows,
 
 void env_update_left(const Sec& ba, const Sec& bb, const std::vector<int>& qn, const SiteMPO& W,
                      const EnvSlab& Lin, const double* A, EnvSlab& Lout, int prec, unsigned* err, cudaStream_t st) {
+    g_prof_class = PROF_ENV;
     const int d = (int)qn.size();
     const SiteLayout S = site_layout(ba, bb, qn);
     const EnvLayout& Li = Lin.lay;
@@ -648,6 +652,7 @@ void env_update_left(const Sec& ba, const Sec& bb, const std::vector<int>& qn, c
 
 void env_update_right(const Sec& ba, const Sec& bc, const std::vector<int>& qn, const SiteMPO& W,
                       const EnvSlab& Rin, const double* Bt, EnvSlab& Rout, int prec, unsigned* err, cudaStream_t st) {
+    g_prof_class = PROF_ENV;
     const int d = (int)qn.size();
     const SiteLayout S = site_layout(ba, bc, qn);
     const EnvLayout& Ri = Rin.lay;
@@ -781,7 +786,7 @@ void form_two_site(const Sec& bl, const Sec& bm, const Sec& br, const std::vecto
         if (!jobs.empty()) {
             k_colscale<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<ColScaleJob>(), left, mid,
                                                                                    scaled.as<double>());
-            PD_CK(cudaGetLastError());
+            PD_LAUNCHED();
         }
         lsrc = scaled.as<double>();
         PD_CK(cudaStreamSynchronize(st));
@@ -985,12 +990,12 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     if (!ja.empty()) {
         k_svd_scatter<<<dim3(gridn(mx, 256), (unsigned)ja.size()), 256, 0, st>>>(
             dja.as<ScatJob>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(), dord.as<int>(), dwts.as<double>(), A_out);
-        PD_CK(cudaGetLastError());
+        PD_LAUNCHED();
     }
     if (!jb.empty()) {
         k_svd_scatter<<<dim3(gridn(mx, 256), (unsigned)jb.size()), 256, 0, st>>>(
             djb.as<ScatJob>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(), dord.as<int>(), dwts.as<double>(), B_out);
-        PD_CK(cudaGetLastError());
+        PD_LAUNCHED();
     }
     // lambda
     std::vector<LamJob> lj;
@@ -1009,7 +1014,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     }
     k_lam_out<<<std::max<int>(1, (int)lj.size()), 128, 0, st>>>(dlj.as<LamJob>(), (int)lj.size(), dsig.as<double>(),
                                                                  dord.as<int>(), dwts.as<double>(), lam_dev);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
     res.lam.resize(o);
     PD_CK(cudaMemcpyAsync(res.lam.data(), lam_dev, o * 8, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
@@ -1063,7 +1068,7 @@ DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, i
     int k = 1;
     launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
     k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
     double hn[4];
     for (int it = 1; it <= max_iter; ++it) {
         res.iters = it;
@@ -1085,7 +1090,7 @@ DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, i
             k = 1;
             launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
             k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
-            PD_CK(cudaGetLastError());
+            PD_LAUNCHED();
         }
         for (int pass = 0; pass < 2; ++pass) {
             launch_dots(V, n, k, dt.as<double>(), n, dpart.as<double>(), nch, dd1.as<double>(), st);
@@ -1104,7 +1109,7 @@ DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, i
         launch_dots(V, n, k + 1, avk, n, dpart.as<double>(), nch, dd1.as<double>(), st);
         launch_dots(AV, n, k, vk, n, dpart.as<double>(), nch, dd2.as<double>(), st);
         k_place<<<1, 32, 0, st>>>(G, kmax, k, dd1.as<double>(), dd2.as<double>());
-        PD_CK(cudaGetLastError());
+        PD_LAUNCHED();
         ++k;
     }
     // x = u / |u|

@@ -1,0 +1,91 @@
+// Process-wide instrumentation: kernel-launch counter and event timing of grouped GEMMs.
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace pd {
+
+std::atomic<long long> g_launches{0};
+thread_local int g_prof_class = PROF_MV;
+
+namespace {
+struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+    double flops;
+};
+std::mutex g_mu;
+std::atomic<bool> g_on{false};
+std::vector<Rec> g_pending;
+double g_ms[3] = {0, 0, 0}, g_fl[3] = {0, 0, 0};
+long long g_n[3] = {0, 0, 0};
+}  // namespace
+
+bool prof_on() { return g_on.load(std::memory_order_relaxed); }
+
+void* prof_start(cudaStream_t st) {
+    cudaEvent_t* ev = new cudaEvent_t[2];
+    PD_CK(cudaEventCreate(&ev[0]));
+    PD_CK(cudaEventCreate(&ev[1]));
+    PD_CK(cudaEventRecord(ev[0], st));
+    return ev;
+}
+
+void prof_stop(void* token, cudaStream_t st, int cls, double flops) {
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(token);
+    PD_CK(cudaEventRecord(ev[1], st));
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pending.push_back({ev[0], ev[1], cls, flops});
+    delete[] ev;
+}
+
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" {
+
+void dmrg_profile_enable(int on) { g_on.store(on != 0); }
+
+void dmrg_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaDeviceSynchronize();
+    for (auto& r : g_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_pending.clear();
+    for (int i = 0; i < 3; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
+    g_launches.store(0);
+}
+
+dmrg_status dmrg_profile_read(dmrg_profile* out) {
+    if (!out) return DMRG_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return DMRG_ERR_CUDA;
+    for (auto& r : g_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_ms[r.cls] += ms;
+            g_fl[r.cls] += r.flops;
+            g_n[r.cls] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_pending.clear();
+    out->launches = g_launches.load();
+    out->mv_gemm_launches = g_n[PROF_MV];
+    out->mv_gemm_ms = g_ms[PROF_MV];
+    out->mv_gemm_flops = g_fl[PROF_MV];
+    out->env_gemm_launches = g_n[PROF_ENV];
+    out->env_gemm_ms = g_ms[PROF_ENV];
+    out->env_gemm_flops = g_fl[PROF_ENV];
+    out->f64_gemm_launches = g_n[PROF_F64];
+    out->f64_gemm_ms = g_ms[PROF_F64];
+    out->f64_gemm_flops = g_fl[PROF_F64];
+    return DMRG_OK;
+}
+
+}  // extern "C"

@@ -368,9 +368,11 @@ void launch_tc(GemmBatch& g, const CUtensorMap& ma, const CUtensorMap& mb, int l
         attr = true;
     }
     int grid = std::min(g.ntiles, sm_count());
+    void* tok = prof_on() ? prof_start(st) : nullptr;
     kern<<<grid, THREADS, SMEM, st>>>(ma, mb, g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles,
                                       lda, ldb, (OutT*)C, err);
-    PD_CK(cudaGetLastError());
+    PD_LAUNCHED();
+    if (tok) prof_stop(tok, st, g_prof_class, g.flops);
 }
 
 // Tile width from the batch's column sizes (fewest padded columns, ties to the wider tile).

@@ -428,3 +428,78 @@ def unpack_site(flat, bl: dict, br: dict, qn):
                 blocks[(ql, s)] = np.asarray(flat[off: off + ml * mr]).reshape(ml, mr)
                 off += ml * mr
     return blocks
+
+
+# ----------------------------------------------------------------------------------------
+# Seeded random mixed-canonical MPS (benchmark states at large m)
+# ----------------------------------------------------------------------------------------
+
+
+def consistent_sectors(bonds, qn):
+    """Shrink sector dims until every sector of bond b is reachable from both neighbours with
+    at least as many states (needed for left/right isometries); drops empty sectors."""
+    bonds = [dict(b) for b in bonds]
+    L = len(bonds) - 1
+    changed = True
+    while changed:
+        changed = False
+        for b in range(1, L + 1):
+            for q in list(bonds[b]):
+                avail = sum(bonds[b - 1].get(q - s, 0) for s in qn)
+                if avail < bonds[b][q]:
+                    changed = True
+                    if avail == 0:
+                        del bonds[b][q]
+                    else:
+                        bonds[b][q] = avail
+        for b in range(L - 1, -1, -1):
+            for q in list(bonds[b]):
+                avail = sum(bonds[b + 1].get(q + s, 0) for s in qn)
+                if avail < bonds[b][q]:
+                    changed = True
+                    if avail == 0:
+                        del bonds[b][q]
+                    else:
+                        bonds[b][q] = avail
+    return bonds
+
+
+def isometric_mps(L, qn, qtot, m, seed, center, sigma=None) -> BlockMPS:
+    """Random MPS in mixed-canonical form around `center`: sites < center are random left
+    isometries, sites > center random right isometries (QR of Gaussian matrices), the centre
+    a normalised Gaussian tensor.  Draws from numpy default_rng(seed), site by site."""
+    rng = np.random.default_rng(seed)
+    bonds = consistent_sectors(bond_sectors(L, qn, qtot, m, sigma), qn)
+    sites = []
+    for j in range(L):
+        bl, br = bonds[j], bonds[j + 1]
+        blocks = {}
+        if j < center:
+            for qr, mr in br.items():
+                rows = [(ql, s) for ql in bl for s, qs in enumerate(qn) if ql + qs == qr]
+                n = sum(bl[ql] for ql, _ in rows)
+                Q, _ = np.linalg.qr(rng.standard_normal((n, mr)))
+                o = 0
+                for (ql, s) in rows:
+                    blocks[(ql, s)] = Q[o: o + bl[ql], :].copy()
+                    o += bl[ql]
+        elif j > center:
+            for ql, ml in bl.items():
+                cols = [(s, ql + qs) for s, qs in enumerate(qn) if (ql + qs) in br]
+                n = sum(br[qr] for _, qr in cols)
+                Q, _ = np.linalg.qr(rng.standard_normal((n, ml)))
+                Bm = Q.T
+                o = 0
+                for (s, qr) in cols:
+                    blocks[(ql, s)] = Bm[:, o: o + br[qr]].copy()
+                    o += br[qr]
+        else:
+            for ql, ml in bl.items():
+                for s, qs in enumerate(qn):
+                    mr = br.get(ql + qs)
+                    if mr:
+                        blocks[(ql, s)] = rng.standard_normal((ml, mr))
+            nrm = math.sqrt(sum(float(np.sum(b * b)) for b in blocks.values()))
+            blocks = {k: v / nrm for k, v in blocks.items()}
+        sites.append(blocks)
+    return BlockMPS(bonds=bonds, sites=sites)
