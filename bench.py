@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--m", type=int, default=2000)
     ap.add_argument("--sigma", type=float, default=5.0)
     ap.add_argument("--dav-iters", type=int, default=4)
+    ap.add_argument("--refine-iters", type=int, default=1)
     ap.add_argument("--kmax", type=int, default=8)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
@@ -263,7 +264,8 @@ def main():
     t_setup = time.perf_counter()
     eng.set_mps(mps.bonds, data, center=center)
     t_setup = time.perf_counter() - t_setup
-    dav = dict(dav_tol=0.0, dav_max_iter=args.dav_iters)     # a fixed number of Davidson steps
+    # a fixed number of Davidson steps: tensor-core iterations, then an FP32-accurate refinement
+    dav = dict(dav_tol=0.0, dav_max_iter=args.dav_iters, refine_iters=args.refine_iters)
     for _ in range(args.warmup):
         eng.advance(1, args.m, **dav)
     torch.cuda.synchronize()
@@ -319,18 +321,24 @@ def main():
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}", "D": max(mpo.D),
                    "m": args.m, "sectors_at_bond": len(mps.bonds[center + 1]), "bond_start": center,
-                   "dav_iters": args.dav_iters, "kmax": args.kmax, "precision": args.precision,
+                   "dav_iters": args.dav_iters, "refine_iters": args.refine_iters, "kmax": args.kmax,
+                   "precision": args.precision,
                    "regions": 1, "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
                    "setup_s": t_setup},
         "sweep_s": ms_step * 2 * (L - 1) / 1e3,
         "sweep_s_note": "bulk step time at m=2000 x 2(L-1) steps",
         "matvecs": sum(s["n_matvec"] for s in stats),
+        "refine_matvecs": sum(s["n_refine_matvec"] for s in stats),
+        "refine_matvec_ms": 1e3 * sum(s["refine_seconds"] for s in stats) / max(1, sum(s["n_refine_matvec"] for s in stats)),
         "matvec_ms": 1e3 * mv_s / max(1, sum(s["n_matvec"] for s in stats)),
         "energy_last_step": stats[-1]["energy"],
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": ctypes.sizeof(pd.SweepParams),
                 "d2h_bytes_per_step": ctypes.sizeof(pd.SweepStats)},
+        "svd": {"calls": prof["svd_calls"], "sweeps_per_call": prof["svd_sweeps"] / max(1, prof["svd_calls"]),
+                "ms_per_call": prof["svd_ms"] / max(1, prof["svd_calls"])},
+        "env_update_ms_per_step": prof["f32_gemm_ms"] / args.steps if args.precision != "fp64" else None,
         "gpu_launches": prof["launches"],
         "clocks": clocks,
     }

@@ -100,7 +100,10 @@ typedef struct {
 typedef struct {
     int m_max;              /* kept states per bond (truncation target m)                     */
     double dav_tol;         /* Davidson stops when |r| <= dav_tol * max(1, |theta|)           */
-    int dav_max_iter;       /* Davidson iteration cap per bond                                */
+    int dav_max_iter;       /* Davidson iteration cap per bond (tensor-core matvec in the
+                               mixed modes)                                                   */
+    int refine_iters;       /* mixed modes only: Davidson iterations continued from the Ritz
+                               vector with an FP32-accurate matvec (0 = none)                 */
 } dmrg_sweep_params;
 
 typedef struct {
@@ -116,6 +119,8 @@ typedef struct {
     double matvec_flops;    /* algorithmic flops of those matvecs (nonzero blocks only)       */
     double min_fidelity;    /* smallest merge fidelity 1-|<Psi'|Psi>| of the sweep (-1: none)  */
     double max_fidelity;    /* largest merge fidelity of the sweep (-1: none)                 */
+    int n_refine_matvec;    /* FP32-accurate refinement matvecs (mixed modes)                 */
+    double refine_seconds;  /* their summed device time                                       */
 } dmrg_sweep_stats;
 
 typedef struct dmrg_ctx dmrg_ctx;
@@ -187,7 +192,9 @@ const char* dmrg_status_string(int status);
 /* ------------------------------------------------------------------------------------------
  * Instrumentation (process-wide).  Kernel launches are always counted; with profiling on, the
  * grouped-GEMM launches are bracketed by CUDA events on their own stream and their device
- * time and algorithmic flops are accumulated per class.
+ * time and algorithmic flops are accumulated per class.  Environment updates run at FP32
+ * accuracy or better in every mode (their rounding errors compound from site to site), so in
+ * the mixed modes they appear under f32_gemm_*.
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
     long long launches;          /* kernels launched by the library since the last reset       */
@@ -200,6 +207,12 @@ typedef struct {
     long long f64_gemm_launches; /* FP64 grouped-GEMM launches (any use)                        */
     double f64_gemm_ms;
     double f64_gemm_flops;
+    long long f32_gemm_launches; /* FP32 SIMT grouped-GEMM launches (mixed-mode environments)   */
+    double f32_gemm_ms;
+    double f32_gemm_flops;
+    long long svd_calls;         /* block-sparse SVDs (one per two-site split)                  */
+    long long svd_sweeps;        /* Jacobi sweeps they ran in total                             */
+    double svd_ms;               /* device time of their Jacobi kernels                         */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);

@@ -38,7 +38,9 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("mv_gemm_launches", C.c_longlong), ("mv_gemm_ms", C.c_double),
                 ("mv_gemm_flops", C.c_double), ("env_gemm_launches", C.c_longlong), ("env_gemm_ms", C.c_double),
                 ("env_gemm_flops", C.c_double), ("f64_gemm_launches", C.c_longlong), ("f64_gemm_ms", C.c_double),
-                ("f64_gemm_flops", C.c_double)]
+                ("f64_gemm_flops", C.c_double), ("f32_gemm_launches", C.c_longlong), ("f32_gemm_ms", C.c_double),
+                ("f32_gemm_flops", C.c_double), ("svd_calls", C.c_longlong), ("svd_sweeps", C.c_longlong),
+                ("svd_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -49,14 +51,15 @@ class Config(C.Structure):
 
 
 class SweepParams(C.Structure):
-    _fields_ = [("m_max", C.c_int), ("dav_tol", C.c_double), ("dav_max_iter", C.c_int)]
+    _fields_ = [("m_max", C.c_int), ("dav_tol", C.c_double), ("dav_max_iter", C.c_int), ("refine_iters", C.c_int)]
 
 
 class SweepStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("max_trunc_err", C.c_double), ("max_m", C.c_int),
                 ("n_matvec", C.c_int), ("n_steps", C.c_int), ("dav_nonconv", C.c_int),
                 ("seconds", C.c_double), ("matvec_seconds", C.c_double), ("matvec_flops", C.c_double),
-                ("min_fidelity", C.c_double), ("max_fidelity", C.c_double)]
+                ("min_fidelity", C.c_double), ("max_fidelity", C.c_double), ("n_refine_matvec", C.c_int),
+                ("refine_seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -225,8 +228,8 @@ class Engine:
         self._h = h
 
     @staticmethod
-    def params(m_max, dav_tol=1e-10, dav_max_iter=100):
-        return SweepParams(int(m_max), float(dav_tol), int(dav_max_iter))
+    def params(m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
+        return SweepParams(int(m_max), float(dav_tol), int(dav_max_iter), int(refine_iters))
 
     def set_mps(self, bonds, site_data, center=None):
         """bonds: list of L+1 dicts charge -> dim; site_data: concatenated packed site tensors.
@@ -240,24 +243,24 @@ class Engine:
                        0 if center is None else 1, 0 if center is None else int(center))
         _check(lib().dmrg_set_mps(self._h, C.byref(desc)), self._h)
 
-    def setup_regions(self, n_regions, warmup, m_max, dav_tol=1e-10, dav_max_iter=100):
-        p = self.params(m_max, dav_tol, dav_max_iter)
+    def setup_regions(self, n_regions, warmup, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
+        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters)
         _check(lib().dmrg_setup_regions(self._h, int(n_regions), int(warmup), C.byref(p)), self._h)
 
-    def sweep(self, m_max, dav_tol=1e-10, dav_max_iter=100):
-        p = self.params(m_max, dav_tol, dav_max_iter)
+    def sweep(self, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
+        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters)
         s = SweepStats()
         _check(lib().dmrg_sweep(self._h, C.byref(p), C.byref(s)), self._h)
         return s.as_dict()
 
-    def advance(self, n_steps, m_max, dav_tol=1e-10, dav_max_iter=100):
-        p = self.params(m_max, dav_tol, dav_max_iter)
+    def advance(self, n_steps, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
+        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters)
         s = SweepStats()
         _check(lib().dmrg_advance(self._h, int(n_steps), C.byref(p), C.byref(s)), self._h)
         return s.as_dict()
 
-    def merge(self, k, m_max, dav_tol=1e-10, dav_max_iter=100):
-        p = self.params(m_max, dav_tol, dav_max_iter)
+    def merge(self, k, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
+        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters)
         f, e = C.c_double(0), C.c_double(0)
         _check(lib().dmrg_merge(self._h, int(k), C.byref(p), C.byref(f), C.byref(e)), self._h)
         return f.value, e.value

@@ -21,8 +21,8 @@ using namespace pd;
 namespace {
 
 struct StepStats {
-    double energy = 0.0, trunc = 0.0, mv_ms = 0.0, mv_flops = 0.0;
-    int m = 0, matvecs = 0, nonconv = 0, steps = 0;
+    double energy = 0.0, trunc = 0.0, mv_ms = 0.0, mv_flops = 0.0, acc_ms = 0.0;
+    int m = 0, matvecs = 0, nonconv = 0, steps = 0, acc_matvecs = 0;
     double fid_min = -1.0, fid_max = -1.0;
     void merge(const StepStats& o) {
         trunc = std::max(trunc, o.trunc);
@@ -32,6 +32,8 @@ struct StepStats {
         steps += o.steps;
         mv_ms += o.mv_ms;
         mv_flops += o.mv_flops;
+        acc_ms += o.acc_ms;
+        acc_matvecs += o.acc_matvecs;
         if (o.fid_min >= 0) fid_min = fid_min < 0 ? o.fid_min : std::min(fid_min, o.fid_min);
         if (o.fid_max >= 0) fid_max = std::max(fid_max, o.fid_max);
     }
@@ -180,10 +182,15 @@ DavResult solve_bond(dmrg_ctx* c, Chain& ch, int j, EnvSlab& Lj, EnvSlab& Rj, DB
     env_make_operand(Lj, c->prec, ch.st);
     env_make_operand(Rj, c->prec, ch.st);
     auto plan = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), Lj.lay, Rj.lay, c->prec, ch.st);
+    std::unique_ptr<HeffPlan> acc;
+    if (c->prec != DMRG_FP64 && p->refine_iters > 0)
+        acc = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), Lj.lay, Rj.lay, PREC_F32, ch.st);
     DavResult r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter,
-                           ch.err.as<unsigned>(), ch.st);
+                           ch.err.as<unsigned>(), ch.st, acc.get(), p->refine_iters);
     s.matvecs += r.matvecs;
     s.mv_ms += r.mv_ms;
+    s.acc_matvecs += r.acc_matvecs;
+    s.acc_ms += r.acc_ms;
     s.mv_flops += plan->flops * r.matvecs;
     if (r.rnorm > p->dav_tol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
     if (flops_per_mv) *flops_per_mv = plan->flops;
@@ -200,8 +207,15 @@ void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_
     DBuf A, B;
     A.ensure(std::max<long long>(1, na) * 8, st);
     B.ensure(std::max<long long>(1, nb) * 8, st);
+    // mixed-precision modes: FP32 Jacobi on ordinary bonds; FP64 at shared (accurate) bonds
+    const bool fp32 = c->prec != DMRG_FP64 && !accurate;
     SplitResult r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
-                              right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st);
+                              right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st, fp32);
+    if (fp32) {
+        // the factor that joins a block must be orthonormal to FP64 accuracy
+        if (right) orthonormalize_factor(bl, r.mid, c->qn, A.as<double>(), true, st);
+        else orthonormalize_factor(r.mid, br, c->qn, B.as<double>(), false, st);
+    }
     ch.bond[j + 1] = r.mid;
     ch.lam[j + 1] = r.lam;
     s.trunc = std::max(s.trunc, r.trunc);
@@ -367,11 +381,16 @@ void do_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fid_out, d
     env_make_operand(Lj, c->prec, st);
     env_make_operand(Rj, c->prec, st);
     auto plan = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, c->prec, st);
+    std::unique_ptr<HeffPlan> accp;
+    if (c->prec != DMRG_FP64 && p->refine_iters > 0)
+        accp = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, PREC_F32, st);
     DavResult r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter,
-                           left.err.as<unsigned>(), st);
+                           left.err.as<unsigned>(), st, accp.get(), p->refine_iters);
     StepStats& s = left.acc;
     s.matvecs += r.matvecs;
     s.mv_ms += r.mv_ms;
+    s.acc_matvecs += r.acc_matvecs;
+    s.acc_ms += r.acc_ms;
     s.mv_flops += plan->flops * r.matvecs;
     if (r.rnorm > p->dav_tol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
     double ov = dot_host(guess.as<double>(), psi.as<double>(), P.size, st);
@@ -709,6 +728,8 @@ dmrg_status dmrg_sweep(dmrg_ctx* c, const dmrg_sweep_params* p, dmrg_sweep_stats
         stats->matvec_flops = tot.mv_flops;
         stats->min_fidelity = tot.fid_min;
         stats->max_fidelity = tot.fid_max;
+        stats->n_refine_matvec = tot.acc_matvecs;
+        stats->refine_seconds = tot.acc_ms * 1e-3;
     }
     return DMRG_OK;
     CTX_CATCH(c)
@@ -743,6 +764,8 @@ dmrg_status dmrg_advance(dmrg_ctx* c, int n_steps, const dmrg_sweep_params* p, d
         stats->matvec_flops = tot.mv_flops;
         stats->min_fidelity = -1.0;
         stats->max_fidelity = -1.0;
+        stats->n_refine_matvec = tot.acc_matvecs;
+        stats->refine_seconds = tot.acc_ms * 1e-3;
     }
     return DMRG_OK;
     CTX_CATCH(c)

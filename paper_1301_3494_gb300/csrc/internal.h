@@ -42,13 +42,15 @@ extern std::atomic<long long> g_launches;
 
 // Profiling classes of grouped-GEMM launches; the class of tensor-core launches comes from the
 // calling thread's current activity.
-enum ProfClass { PROF_MV = 0, PROF_ENV = 1, PROF_F64 = 2 };
+enum ProfClass { PROF_MV = 0, PROF_ENV = 1, PROF_F64 = 2, PROF_F32 = 3 };
 extern thread_local int g_prof_class;
 bool prof_on();
 // With profiling on: record an event pair around a launch (call prof_start before the launch,
 // prof_stop after); the elapsed time is resolved in dmrg_profile_read.
 void* prof_start(cudaStream_t st);
 void prof_stop(void* token, cudaStream_t st, int cls, double flops);
+// Jacobi SVD statistics (sweeps run per call), accumulated while profiling is on.
+void prof_svd(int sweeps, double ms);
 
 // Device error word bits (written by kernels, read by the host after a step).
 enum : unsigned {
@@ -121,20 +123,32 @@ struct DiagTerm {
 // ------------------------------------------------------------------------------------------
 // Launch wrappers (kernels.cu)
 // ------------------------------------------------------------------------------------------
-void launch_gemm64(const GProb* probs, const GSeg* segs, const GTile* tiles, int ntiles,
-                   const double* A, const double* B, double* C, cudaStream_t st);
+template <class T>
+void launch_gemm_simt(const GProb* probs, const GSeg* segs, const GTile* tiles, int ntiles, const T* A, const T* B,
+                      T* C, cudaStream_t st);
 
+// Elementwise block kernels run one CTA per chunk of CHUNK elements of one job; `chunks`
+// lists (job, first element) for every chunk (built on the host, see make_chunks).
+constexpr int CHUNK = 2048;
 template <class Tin, class Tout>
-void launch_copy(const CopyJob* jobs, int njobs, int max_elems, const Tin* src, Tout* dst,
+void launch_copy(const CopyJob* jobs, const int2* chunks, int nchunks, const Tin* src, Tout* dst,
                  cudaStream_t st);
 
 template <class Tin, class Tout>
-void launch_mix(const MixJob* jobs, int njobs, int max_elems, const MixTerm* terms,
+void launch_mix(const MixJob* jobs, const int2* chunks, int nchunks, const MixTerm* terms,
                 const Tin* in, Tout* out, cudaStream_t st);
 
 template <class T>
-void launch_diag(const DiagJob* jobs, int njobs, int max_elems, const DiagTerm* terms,
+void launch_diag(const DiagJob* jobs, const int2* chunks, int nchunks, const DiagTerm* terms,
                  const T* Lslab, int ldl, const T* Rslab, int ldr, double* out, cudaStream_t st);
+
+// Chunk table for jobs of the given element counts.
+inline std::vector<int2> make_chunks(const std::vector<long long>& elems) {
+    std::vector<int2> c;
+    for (size_t j = 0; j < elems.size(); ++j)
+        for (long long e = 0; e < elems[j]; e += CHUNK) c.push_back(make_int2((int)j, (int)e));
+    return c;
+}
 
 // Davidson helpers (all FP64, vectors of length n, basis rows of stride ldv)
 void launch_dots(const double* V, long long ldv, int k, const double* y, long long n,
@@ -162,15 +176,21 @@ struct SvdSec {
     int npad;             // n rounded up to even
     int pair0;            // first global pair index of this sector in a round
 };
-void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, double* V, cudaStream_t st);
-void launch_jacobi_round(const SvdSec* secs, const int* pair_sec, int npairs, int round,
-                         double* W, double* V, double tol, int* rotated, cudaStream_t st);
-void launch_svd_finish(const SvdSec* secs, int nsec, int max_n, const double* W, double* sig,
-                       int* order, cudaStream_t st);
+template <class T>
+void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, T* V, cudaStream_t st);
+// All Jacobi sweeps (until a sweep without rotation, at most max_sweeps) in one cooperative launch.
+// Pairs whose smaller column norm is below eta * |W_sector|_F are not rotated (eta = 0: all are).
+// floor2: nsec doubles of scratch.
+template <class T>
+void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs, int maxnpad, int max_sweeps, T* W,
+                   T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, cudaStream_t st);
+template <class T>
+void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st);
 
-// Truncation selection over all sectors (single CTA).  sig sorted per sector by `order`.
-void launch_truncate(const SvdSec* secs, int nsec, const double* sig, const int* order,
-                     int total, int m_max, double rel_cutoff, double degen_tol, int* kept,
-                     double* weights, cudaStream_t st);
+// Truncation selection over all sectors.  sig sorted per sector by `order`; sectors packed
+// back to back (s_off = prefix sums).  Scratch: (total + nsec) doubles, 3*total ints.
+void launch_truncate(const SvdSec* secs, int nsec, const double* sig, const int* order, int total, int m_max,
+                     double rel_cutoff, double degen_tol, int* kept, double* weights, double* scratch_d, int* scratch_i,
+                     cudaStream_t st);
 
 }  // namespace pd

@@ -7,10 +7,15 @@
 //  * Davidson       dot products, Ritz vectors, residuals, Gram-Schmidt, small Jacobi eigensolver
 //  * SVD            batched one-sided (Hestenes) Jacobi SVD per charge sector, Eq. (svd)
 //  * truncation     global keep-largest-m selection over all sectors (single CTA)
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace pd {
 
@@ -52,32 +57,34 @@ __device__ double block_sum(double v) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Grouped FP64 GEMM: 64x64 output tile per CTA, 256 threads, 4x4 per thread, K chunks of 16.
+// Grouped SIMT GEMM (FP64 or FP32): 64x64 output tile per CTA, 256 threads, 4x4 per thread,
+// K chunks of 16.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gemm64(const GProb* __restrict__ probs,
-                                                const GSeg* __restrict__ segs,
-                                                const GTile* __restrict__ tiles,
-                                                const double* __restrict__ A,
-                                                const double* __restrict__ B,
-                                                double* __restrict__ C) {
-    __shared__ double As[16][65];
-    __shared__ double Bs[16][65];
+template <class T>
+__global__ void __launch_bounds__(256) k_gemm_simt(const GProb* __restrict__ probs,
+                                                   const GSeg* __restrict__ segs,
+                                                   const GTile* __restrict__ tiles,
+                                                   const T* __restrict__ A,
+                                                   const T* __restrict__ B,
+                                                   T* __restrict__ C) {
+    __shared__ T As[16][65];
+    __shared__ T Bs[16][65];
     const GTile t = tiles[blockIdx.x];
     const GProb p = probs[t.prob];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     for (int sgi = 0; sgi < p.nseg; ++sgi) {
         const GSeg sg = segs[p.seg0 + sgi];
         for (int k0 = 0; k0 < sg.K; k0 += 16) {
             for (int e = tid; e < 1024; e += 256) {
                 int kk = e & 15, mm = e >> 4;
                 int m = t.m0 + mm, k = k0 + kk;
-                double va = 0.0, vb = 0.0;
+                T va = T(0), vb = T(0);
                 if (m < p.M && k < sg.K) va = A[sg.a_off + (long long)m * p.sam + (long long)k * p.sak];
                 int n = t.n0 + mm;
                 if (n < p.N && k < sg.K) vb = B[sg.b_off + (long long)n * p.sbn + (long long)k * p.sbk];
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(256) k_gemm64(const GProb* __restrict__ probs,
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
-                double a[4], b[4];
+                T a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(256) k_gemm64(const GProb* __restrict__ probs,
             int n = t.n0 + tx + 16 * j;
             if (n >= p.N) continue;
             long long idx = p.c_off + (long long)m * p.scm + (long long)n * p.scn;
-            double v = p.alpha * acc[i][j];
+            T v = (T)p.alpha * acc[i][j];
             if (p.accumulate) v += C[idx];
             C[idx] = v;
         }
@@ -120,13 +127,14 @@ __global__ void __launch_bounds__(256) k_gemm64(const GProb* __restrict__ probs,
 // Block copies, MPO channel mixing, diagonal
 // ------------------------------------------------------------------------------------------
 template <class Tin, class Tout>
-__global__ void k_copy(const CopyJob* __restrict__ jobs, const Tin* __restrict__ src,
+__global__ void k_copy(const CopyJob* __restrict__ jobs, const int2* __restrict__ chunks, const Tin* __restrict__ src,
                        Tout* __restrict__ dst) {
-    const CopyJob j = jobs[blockIdx.y];
+    const int2 ch = chunks[blockIdx.x];
+    const CopyJob j = jobs[ch.x];
     const int w = j.cols > j.zero_to ? j.cols : j.zero_to;
     const long long total = (long long)j.rows * w;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    const long long end = min(total, (long long)ch.y + CHUNK);
+    for (long long e = (long long)ch.y + threadIdx.x; e < end; e += blockDim.x) {
         int r = (int)(e / w), c = (int)(e % w);
         double v = 0.0;
         if (c < j.cols) v = j.scale * to_d(src[j.src + (long long)r * j.srs + (long long)c * j.scs]);
@@ -135,13 +143,14 @@ __global__ void k_copy(const CopyJob* __restrict__ jobs, const Tin* __restrict__
 }
 
 template <class Tin, class Tout>
-__global__ void k_mix(const MixJob* __restrict__ jobs, const MixTerm* __restrict__ terms,
+__global__ void k_mix(const MixJob* __restrict__ jobs, const int2* __restrict__ chunks, const MixTerm* __restrict__ terms,
                       const Tin* __restrict__ in, Tout* __restrict__ out) {
-    const MixJob j = jobs[blockIdx.y];
+    const int2 ch = chunks[blockIdx.x];
+    const MixJob j = jobs[ch.x];
     const int w = j.cols > j.zero_to ? j.cols : j.zero_to;
     const long long total = (long long)j.rows * w;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    const long long end = min(total, (long long)ch.y + CHUNK);
+    for (long long e = (long long)ch.y + threadIdx.x; e < end; e += blockDim.x) {
         int r = (int)(e / w), c = (int)(e % w);
         double v = 0.0;
         if (c < j.cols) {
@@ -155,13 +164,14 @@ __global__ void k_mix(const MixJob* __restrict__ jobs, const MixTerm* __restrict
 }
 
 template <class T>
-__global__ void k_diag(const DiagJob* __restrict__ jobs, const DiagTerm* __restrict__ terms,
+__global__ void k_diag(const DiagJob* __restrict__ jobs, const int2* __restrict__ chunks, const DiagTerm* __restrict__ terms,
                        const T* __restrict__ Ls, int ldl, const T* __restrict__ Rs, int ldr,
                        double* __restrict__ out) {
-    const DiagJob j = jobs[blockIdx.y];
+    const int2 ch = chunks[blockIdx.x];
+    const DiagJob j = jobs[ch.x];
     const long long total = (long long)j.rows * j.cols;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    const long long end = min(total, (long long)ch.y + CHUNK);
+    for (long long e = (long long)ch.y + threadIdx.x; e < end; e += blockDim.x) {
         int a = (int)(e / j.cols), c = (int)(e % j.cols);
         double v = 0.0;
         for (int t = 0; t < j.nt; ++t) {
@@ -306,14 +316,17 @@ __global__ void k_small_eig(const double* __restrict__ G, int k, int ldg, double
 }
 
 // ------------------------------------------------------------------------------------------
-// One-sided Jacobi SVD
+// One-sided Jacobi SVD (Hestenes).  W holds the sector matrix column-major (p x n, n <= p); pairs
+// of columns are rotated until mutually orthogonal; V accumulates the rotations.  The rounds of
+// a sweep follow the round-robin tournament (n/2 disjoint pairs per round, n-1 rounds).
 // ------------------------------------------------------------------------------------------
-__global__ void k_svd_init_v(const SvdSec* __restrict__ secs, double* __restrict__ V) {
+template <class T>
+__global__ void k_svd_init_v(const SvdSec* __restrict__ secs, T* __restrict__ V) {
     const SvdSec s = secs[blockIdx.y];
     const long long total = (long long)s.n * s.n;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         int c = (int)(e / s.n), r = (int)(e % s.n);
-        V[s.v_off + e] = (r == c) ? 1.0 : 0.0;
+        V[s.v_off + e] = (r == c) ? T(1) : T(0);
     }
 }
 
@@ -322,60 +335,150 @@ __device__ __forceinline__ int rr_player(int pos, int round, int npad) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (npad - 1)) + 1;
 }
 
-__global__ void k_jacobi_round(const SvdSec* __restrict__ secs, const int* __restrict__ pair_sec,
-                               int npairs, int round, double* __restrict__ W, double* __restrict__ V,
-                               double tol, int* __restrict__ rotated) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= npairs) return;
-    const int si = pair_sec[warp];
-    const SvdSec s = secs[si];
-    const int pi = warp - s.pair0;
-    if (round >= s.npad - 1) return;
+template <class T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp rotates one column pair; returns true if it rotated.  Each lane keeps its share of
+// both columns (rows lane, lane+32, ...) in registers, so every phase costs one memory latency.
+constexpr int JREG = 32;   // register-resident rows per lane: p and n up to 32*32 = 1024
+template <class T>
+__device__ __forceinline__ bool jacobi_pair(const SvdSec& s, int pi, int round, T* __restrict__ W,
+                                            T* __restrict__ V, T tol, T floor_, int lane) {
+    if (round >= s.npad - 1) return false;
     int i = rr_player(pi, round, s.npad);
     int j = rr_player(s.npad - 1 - pi, round, s.npad);
     if (i > j) { int t = i; i = j; j = t; }
-    if (j >= s.n) return;                      // bye against the padding column
-    double* ci = W + s.w_off + (long long)i * s.p;
-    double* cj = W + s.w_off + (long long)j * s.p;
-    double al = 0.0, be = 0.0, ga = 0.0;
+    if (j >= s.n) return false;                      // bye against the padding column
+    T* ci = W + s.w_off + (long long)i * s.p;
+    T* cj = W + s.w_off + (long long)j * s.p;
+    T* vi = V + s.v_off + (long long)i * s.n;
+    T* vj = V + s.v_off + (long long)j * s.n;
+    T al = 0, be = 0, ga = 0;
+    if (s.p <= 32 * JREG && s.n <= 32 * JREG) {
+        T x[JREG], y[JREG];
+#pragma unroll
+        for (int k = 0; k < JREG; ++k) {
+            const int r = lane + 32 * k;
+            x[k] = r < s.p ? ci[r] : T(0);
+            y[k] = r < s.p ? cj[r] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < JREG; ++k) {
+            al = fma(x[k], x[k], al);
+            be = fma(y[k], y[k], be);
+            ga = fma(x[k], y[k], ga);
+        }
+        al = wsum(al);
+        be = wsum(be);
+        ga = wsum(ga);
+        if (ga == T(0) || !(fabs(ga) > tol * sqrt(al * be)) || fmin(al, be) <= floor_) return false;
+        T zeta = (be - al) / (T(2) * ga);
+        T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+        T u[JREG], w[JREG];
+#pragma unroll
+        for (int k = 0; k < JREG; ++k) {
+            const int r = lane + 32 * k;
+            u[k] = r < s.n ? vi[r] : T(0);
+            w[k] = r < s.n ? vj[r] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < JREG; ++k) {
+            const int r = lane + 32 * k;
+            if (r < s.p) {
+                ci[r] = c * x[k] - sn * y[k];
+                cj[r] = sn * x[k] + c * y[k];
+            }
+            if (r < s.n) {
+                vi[r] = c * u[k] - sn * w[k];
+                vj[r] = sn * u[k] + c * w[k];
+            }
+        }
+        return true;
+    }
     for (int r = lane; r < s.p; r += 32) {
-        double x = ci[r], y = cj[r];
+        T x = ci[r], y = cj[r];
         al = fma(x, x, al);
         be = fma(y, y, be);
         ga = fma(x, y, ga);
     }
-    al = warp_sum(al);
-    be = warp_sum(be);
-    ga = warp_sum(ga);
-    if (ga == 0.0 || !(fabs(ga) > tol * sqrt(al * be))) return;
-    double zeta = (be - al) / (2.0 * ga);
-    double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+    al = wsum(al);
+    be = wsum(be);
+    ga = wsum(ga);
+    if (ga == T(0) || !(fabs(ga) > tol * sqrt(al * be)) || fmin(al, be) <= floor_) return false;
+    T zeta = (be - al) / (T(2) * ga);
+    T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
     for (int r = lane; r < s.p; r += 32) {
-        double x = ci[r], y = cj[r];
+        T x = ci[r], y = cj[r];
         ci[r] = c * x - sn * y;
         cj[r] = sn * x + c * y;
     }
-    double* vi = V + s.v_off + (long long)i * s.n;
-    double* vj = V + s.v_off + (long long)j * s.n;
     for (int r = lane; r < s.n; r += 32) {
-        double x = vi[r], y = vj[r];
+        T x = vi[r], y = vj[r];
         vi[r] = c * x - sn * y;
         vj[r] = sn * x + c * y;
     }
-    if (lane == 0) atomicOr(rotated, 1);
+    return true;
 }
 
-// sig[s_off + i] = |W_i|, order[s_off + r] = column with the r-th largest norm (ties: lower index).
-__global__ void k_svd_finish(const SvdSec* __restrict__ secs, const double* __restrict__ W,
-                             double* __restrict__ sig, int* __restrict__ order) {
+// All sweeps of all sectors in one cooperative launch; grid-wide sync between rounds.
+// rot[sweep] counts the rotations of that sweep (zeroed by the host); *sweeps = sweeps run.
+template <class T>
+__global__ void k_jacobi_coop(const SvdSec* __restrict__ secs, const int* __restrict__ pair_sec, int npairs,
+                              int maxnpad, int max_sweeps, T* __restrict__ W, T* __restrict__ V, T tol,
+                              const double* __restrict__ floor2, int* __restrict__ rot, int* __restrict__ sweeps) {
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int mine = 0;
+        for (int round = 0; round < maxnpad - 1; ++round) {
+            for (int w = gw; w < npairs; w += nw) {
+                const int si = pair_sec[w];
+                const SvdSec s = secs[si];
+                if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, (T)floor2[si], lane)) mine = 1;
+            }
+            grid.sync();
+        }
+        if (lane == 0 && mine) atomicAdd(&rot[sweep], 1);
+        grid.sync();
+        if (*((volatile int*)&rot[sweep]) == 0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = sweep + 1;
+}
+
+// floor2[s] = (eta * |W_s|_F)^2: columns below it are left unrotated (below working precision).
+template <class T>
+__global__ void k_svd_floor(const SvdSec* __restrict__ secs, const T* __restrict__ W, double eta,
+                            double* __restrict__ floor2) {
+    const SvdSec s = secs[blockIdx.x];
+    double a = 0.0;
+    const long long total = (long long)s.p * s.n;
+    for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+        double x = (double)W[s.w_off + e];
+        a = fma(x, x, a);
+    }
+    a = block_sum(a);
+    if (threadIdx.x == 0) floor2[blockIdx.x] = eta * eta * a;
+}
+
+// sig[s_off + i] = |W_i| (FP64), order[s_off + r] = column with the r-th largest norm (ties: lower index).
+template <class T>
+__global__ void k_svd_finish(const SvdSec* __restrict__ secs, const T* __restrict__ W, double* __restrict__ sig,
+                             int* __restrict__ order) {
     const SvdSec s = secs[blockIdx.x];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = wid; c < s.n; c += nw) {
-        const double* col = W + s.w_off + (long long)c * s.p;
+        const T* col = W + s.w_off + (long long)c * s.p;
         double a = 0.0;
-        for (int r = lane; r < s.p; r += 32) a = fma(col[r], col[r], a);
+        for (int r = lane; r < s.p; r += 32) a = fma((double)col[r], (double)col[r], a);
         a = warp_sum(a);
         if (lane == 0) sig[s.s_off + c] = sqrt(a);
     }
@@ -392,75 +495,88 @@ __global__ void k_svd_finish(const SvdSec* __restrict__ secs, const double* __re
 }
 
 // ------------------------------------------------------------------------------------------
-// Truncation selection (one CTA).  Keys (lambda desc, sector asc, position asc).
-// kept[s] = kept count of sector s; weights[0] = total sum lambda^2, weights[1] = kept sum.
+// Truncation selection.  Keys (lambda desc, sector asc, position asc) over all sectors' values.
+//   k_trunc_flat   flat arrays lam[g], sec[g], pos[g] (sector order, descending inside)
+//   k_trunc_rank   rank of every candidate (lambda > rel_cutoff * lambda_max) among candidates
+//   k_trunc_count  kept[s] and weights: total sum lambda^2, kept sum lambda^2
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_truncate(const SvdSec* __restrict__ secs, int nsec,
-                                                   const double* __restrict__ sig, const int* __restrict__ order,
-                                                   int total, int m_max, double rel_cutoff, double degen_tol,
-                                                   int* __restrict__ kept, double* __restrict__ weights) {
-    extern __shared__ unsigned char smem[];
-    double* lam = reinterpret_cast<double*>(smem);
-    int* sec = reinterpret_cast<int*>(lam + total);
-    int* pos = sec + total;
-    int* rk = pos + total;
-    __shared__ double s_lmax, s_next;
-    __shared__ int s_kept_cnt[256];
-    __shared__ double red[32];
-    // flatten: sector s occupies [s_off, s_off + n) (sectors packed back to back)
-    for (int s = 0; s < nsec; ++s) {
-        const SvdSec S = secs[s];
-        for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
-            lam[S.s_off + i] = sig[S.s_off + order[S.s_off + i]];
-            sec[S.s_off + i] = s;
-            pos[S.s_off + i] = i;
-        }
-    }
-    for (int s = threadIdx.x; s < 256; s += blockDim.x) s_kept_cnt[s] = 0;
-    __syncthreads();
-    double mx = 0.0, tot = 0.0;
-    for (int g = threadIdx.x; g < total; g += blockDim.x) {
-        mx = fmax(mx, lam[g]);
-        tot += lam[g] * lam[g];
+__global__ void k_trunc_flat(const SvdSec* __restrict__ secs, int nsec, const double* __restrict__ sig,
+                             const int* __restrict__ order, double* __restrict__ lam, int* __restrict__ sec,
+                             int* __restrict__ pos, double* __restrict__ lmax) {
+    const int s = blockIdx.x;
+    const SvdSec S = secs[s];
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
+        double v = sig[S.s_off + order[S.s_off + i]];
+        lam[S.s_off + i] = v;
+        sec[S.s_off + i] = s;
+        pos[S.s_off + i] = i;
+        mx = fmax(mx, v);
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double red[32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-        s_lmax = m;
-        s_next = -1.0;
+        lmax[s] = m;
     }
-    tot = block_sum(tot);          // contains __syncthreads, s_lmax visible afterwards
-    const double thr = rel_cutoff * s_lmax;
-    for (int g = threadIdx.x; g < total; g += blockDim.x) {
-        const double v = lam[g];
-        int rank = -1;
-        if (v > thr) {
-            rank = 0;
-            for (int o = 0; o < total; ++o) {
-                const double w = lam[o];
-                if (!(w > thr)) continue;
-                rank += (w > v) || (w == v && (sec[o] < sec[g] || (sec[o] == sec[g] && pos[o] < pos[g])));
-            }
-            if (rank == m_max) s_next = v;
-        }
-        rk[g] = rank;
+}
+
+__global__ void k_trunc_rank(const double* __restrict__ lam, const int* __restrict__ sec, const int* __restrict__ pos,
+                             int total, const double* __restrict__ lmax_sec, int nsec, double rel_cutoff,
+                             int* __restrict__ rank) {
+    __shared__ double thr_s;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int s = 0; s < nsec; ++s) m = fmax(m, lmax_sec[s]);
+        thr_s = rel_cutoff * m;
     }
     __syncthreads();
+    const double thr = thr_s;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const double v = lam[g];
+    const int sg = sec[g], pg = pos[g];
+    int r = -1;
+    if (v > thr) {
+        r = 0;
+        for (int o = 0; o < total; ++o) {
+            const double w = lam[o];
+            r += (w > thr) && ((w > v) || (w == v && (sec[o] < sg || (sec[o] == sg && pos[o] < pg))));
+        }
+    }
+    rank[g] = r;
+}
+
+__global__ void __launch_bounds__(1024) k_trunc_count(const double* __restrict__ lam, const int* __restrict__ sec,
+                                                      const int* __restrict__ rank, int total, int nsec, int m_max,
+                                                      double degen_tol, int* __restrict__ kept,
+                                                      double* __restrict__ weights) {
+    __shared__ double s_next;
+    __shared__ int s_cnt[256];
+    if (threadIdx.x == 0) s_next = -1.0;
+    for (int s = threadIdx.x; s < 256; s += blockDim.x) s_cnt[s] = 0;
+    __syncthreads();
+    double tot = 0.0;
+    for (int g = threadIdx.x; g < total; g += blockDim.x) {
+        tot += lam[g] * lam[g];
+        if (rank[g] == m_max) s_next = lam[g];
+    }
+    tot = block_sum(tot);
     const double nxt = s_next;
     double kw = 0.0;
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
-        const int r = rk[g];
+        const int r = rank[g];
         const double a = lam[g];
         if (r >= 0 && r < m_max && (nxt < 0.0 || a > nxt * (1.0 + degen_tol))) {
             kw += a * a;
-            atomicAdd(&s_kept_cnt[sec[g]], 1);
+            atomicAdd(&s_cnt[sec[g]], 1);
         }
     }
     kw = block_sum(kw);
-    for (int s = threadIdx.x; s < nsec; s += blockDim.x) kept[s] = s_kept_cnt[s];
+    for (int s = threadIdx.x; s < nsec; s += blockDim.x) kept[s] = s_cnt[s];
     if (threadIdx.x == 0) {
         weights[0] = tot;
         weights[1] = kw;
@@ -479,53 +595,52 @@ inline int grid_for(long long elems, int cap = 4096) {
 // ------------------------------------------------------------------------------------------
 // Launch wrappers
 // ------------------------------------------------------------------------------------------
-void launch_gemm64(const GProb* probs, const GSeg* segs, const GTile* tiles, int ntiles,
-                   const double* A, const double* B, double* C, cudaStream_t st) {
+template <class T>
+void launch_gemm_simt(const GProb* probs, const GSeg* segs, const GTile* tiles, int ntiles, const T* A, const T* B,
+                      T* C, cudaStream_t st) {
     if (ntiles <= 0) return;
-    k_gemm64<<<ntiles, 256, 0, st>>>(probs, segs, tiles, A, B, C);
+    k_gemm_simt<T><<<ntiles, 256, 0, st>>>(probs, segs, tiles, A, B, C);
+    PD_LAUNCHED();
+}
+template void launch_gemm_simt<double>(const GProb*, const GSeg*, const GTile*, int, const double*, const double*,
+                                       double*, cudaStream_t);
+template void launch_gemm_simt<float>(const GProb*, const GSeg*, const GTile*, int, const float*, const float*,
+                                      float*, cudaStream_t);
+
+template <class Tin, class Tout>
+void launch_copy(const CopyJob* jobs, const int2* chunks, int nchunks, const Tin* src, Tout* dst, cudaStream_t st) {
+    if (nchunks <= 0) return;
+    k_copy<Tin, Tout><<<nchunks, 256, 0, st>>>(jobs, chunks, src, dst);
     PD_LAUNCHED();
 }
 
 template <class Tin, class Tout>
-void launch_copy(const CopyJob* jobs, int njobs, int max_elems, const Tin* src, Tout* dst, cudaStream_t st) {
-    if (njobs <= 0) return;
-    PD_REQUIRE(njobs <= 65535, DMRG_ERR_CAPACITY, "too many copy jobs in one launch");
-    dim3 g(grid_for(max_elems, 512), njobs);
-    k_copy<Tin, Tout><<<g, 256, 0, st>>>(jobs, src, dst);
-    PD_LAUNCHED();
-}
-
-template <class Tin, class Tout>
-void launch_mix(const MixJob* jobs, int njobs, int max_elems, const MixTerm* terms, const Tin* in,
+void launch_mix(const MixJob* jobs, const int2* chunks, int nchunks, const MixTerm* terms, const Tin* in,
                 Tout* out, cudaStream_t st) {
-    if (njobs <= 0) return;
-    PD_REQUIRE(njobs <= 65535, DMRG_ERR_CAPACITY, "too many mix jobs in one launch");
-    dim3 g(grid_for(max_elems, 512), njobs);
-    k_mix<Tin, Tout><<<g, 256, 0, st>>>(jobs, terms, in, out);
+    if (nchunks <= 0) return;
+    k_mix<Tin, Tout><<<nchunks, 256, 0, st>>>(jobs, chunks, terms, in, out);
     PD_LAUNCHED();
 }
 
 template <class T>
-void launch_diag(const DiagJob* jobs, int njobs, int max_elems, const DiagTerm* terms, const T* Ls, int ldl,
+void launch_diag(const DiagJob* jobs, const int2* chunks, int nchunks, const DiagTerm* terms, const T* Ls, int ldl,
                  const T* Rs, int ldr, double* out, cudaStream_t st) {
-    if (njobs <= 0) return;
-    PD_REQUIRE(njobs <= 65535, DMRG_ERR_CAPACITY, "too many diagonal jobs in one launch");
-    dim3 g(grid_for(max_elems, 512), njobs);
-    k_diag<T><<<g, 256, 0, st>>>(jobs, terms, Ls, ldl, Rs, ldr, out);
+    if (nchunks <= 0) return;
+    k_diag<T><<<nchunks, 256, 0, st>>>(jobs, chunks, terms, Ls, ldl, Rs, ldr, out);
     PD_LAUNCHED();
 }
 
-template void launch_copy<double, double>(const CopyJob*, int, int, const double*, double*, cudaStream_t);
-template void launch_copy<double, float>(const CopyJob*, int, int, const double*, float*, cudaStream_t);
-template void launch_copy<double, __nv_bfloat16>(const CopyJob*, int, int, const double*, __nv_bfloat16*, cudaStream_t);
-template void launch_copy<float, double>(const CopyJob*, int, int, const float*, double*, cudaStream_t);
-template void launch_copy<float, float>(const CopyJob*, int, int, const float*, float*, cudaStream_t);
-template void launch_copy<float, __nv_bfloat16>(const CopyJob*, int, int, const float*, __nv_bfloat16*, cudaStream_t);
-template void launch_mix<double, double>(const MixJob*, int, int, const MixTerm*, const double*, double*, cudaStream_t);
-template void launch_mix<float, float>(const MixJob*, int, int, const MixTerm*, const float*, float*, cudaStream_t);
-template void launch_mix<float, __nv_bfloat16>(const MixJob*, int, int, const MixTerm*, const float*, __nv_bfloat16*, cudaStream_t);
-template void launch_diag<double>(const DiagJob*, int, int, const DiagTerm*, const double*, int, const double*, int, double*, cudaStream_t);
-template void launch_diag<float>(const DiagJob*, int, int, const DiagTerm*, const float*, int, const float*, int, double*, cudaStream_t);
+template void launch_copy<double, double>(const CopyJob*, const int2*, int, const double*, double*, cudaStream_t);
+template void launch_copy<double, float>(const CopyJob*, const int2*, int, const double*, float*, cudaStream_t);
+template void launch_copy<double, __nv_bfloat16>(const CopyJob*, const int2*, int, const double*, __nv_bfloat16*, cudaStream_t);
+template void launch_copy<float, double>(const CopyJob*, const int2*, int, const float*, double*, cudaStream_t);
+template void launch_copy<float, float>(const CopyJob*, const int2*, int, const float*, float*, cudaStream_t);
+template void launch_copy<float, __nv_bfloat16>(const CopyJob*, const int2*, int, const float*, __nv_bfloat16*, cudaStream_t);
+template void launch_mix<double, double>(const MixJob*, const int2*, int, const MixTerm*, const double*, double*, cudaStream_t);
+template void launch_mix<float, float>(const MixJob*, const int2*, int, const MixTerm*, const float*, float*, cudaStream_t);
+template void launch_mix<float, __nv_bfloat16>(const MixJob*, const int2*, int, const MixTerm*, const float*, __nv_bfloat16*, cudaStream_t);
+template void launch_diag<double>(const DiagJob*, const int2*, int, const DiagTerm*, const double*, int, const double*, int, double*, cudaStream_t);
+template void launch_diag<float>(const DiagJob*, const int2*, int, const DiagTerm*, const float*, int, const float*, int, double*, cudaStream_t);
 
 void launch_dots(const double* V, long long ldv, int k, const double* y, long long n, double* partial,
                  int nchunks, double* out, cudaStream_t st) {
@@ -576,37 +691,65 @@ void launch_finite_check(const double* x, long long n, unsigned* err, cudaStream
     PD_LAUNCHED();
 }
 
-void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, double* V, cudaStream_t st) {
+template <class T>
+void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, T* V, cudaStream_t st) {
     if (nsec <= 0) return;
-    k_svd_init_v<<<dim3(grid_for((long long)max_n * max_n, 256), nsec), 256, 0, st>>>(secs, V);
+    k_svd_init_v<T><<<dim3(grid_for((long long)max_n * max_n, 256), nsec), 256, 0, st>>>(secs, V);
     PD_LAUNCHED();
 }
+template void launch_svd_init_v<double>(const SvdSec*, int, int, double*, cudaStream_t);
+template void launch_svd_init_v<float>(const SvdSec*, int, int, float*, cudaStream_t);
 
-void launch_jacobi_round(const SvdSec* secs, const int* pair_sec, int npairs, int round, double* W, double* V,
-                         double tol, int* rotated, cudaStream_t st) {
-    if (npairs <= 0) return;
-    int warps_per_block = 8;
-    int blocks = (npairs + warps_per_block - 1) / warps_per_block;
-    k_jacobi_round<<<blocks, 32 * warps_per_block, 0, st>>>(secs, pair_sec, npairs, round, W, V, tol, rotated);
+template <class T>
+void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs, int maxnpad, int max_sweeps, T* W,
+                   T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, cudaStream_t st) {
+    if (npairs <= 0 || maxnpad < 2) return;
+    k_svd_floor<T><<<nsec, 256, 0, st>>>(secs, W, eta, floor2);
+    PD_LAUNCHED();
+    const int threads = 128;   // register-heavy pair updates: small blocks keep several per SM
+    static int per_sm[2] = {0, 0};
+    int& ps = per_sm[sizeof(T) == 8 ? 1 : 0];
+    if (!ps) PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_jacobi_coop<T>, threads, 0));
+    int dev = 0, sms = 0;
+    PD_CK(cudaGetDevice(&dev));
+    PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int need = (npairs * 32 + threads - 1) / threads;
+    int blocks = std::max(1, std::min(need, ps * sms));
+    const double* fl = floor2;
+    void* args[] = {(void*)&secs, (void*)&pair_sec, (void*)&npairs, (void*)&maxnpad, (void*)&max_sweeps,
+                    (void*)&W, (void*)&V, (void*)&tol, (void*)&fl, (void*)&rot, (void*)&sweeps};
+    PD_CK(cudaLaunchCooperativeKernel((void*)k_jacobi_coop<T>, blocks, threads, args, 0, st));
     PD_LAUNCHED();
 }
+template void launch_jacobi<double>(const SvdSec*, int, const int*, int, int, int, double*, double*, double, double,
+                                    double*, int*, int*, cudaStream_t);
+template void launch_jacobi<float>(const SvdSec*, int, const int*, int, int, int, float*, float*, float, double,
+                                   double*, int*, int*, cudaStream_t);
 
-void launch_svd_finish(const SvdSec* secs, int nsec, int max_n, const double* W, double* sig, int* order,
-                       cudaStream_t st) {
+template <class T>
+void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st) {
     if (nsec <= 0) return;
-    (void)max_n;
-    k_svd_finish<<<nsec, 256, 0, st>>>(secs, W, sig, order);
+    k_svd_finish<T><<<nsec, 256, 0, st>>>(secs, W, sig, order);
     PD_LAUNCHED();
 }
+template void launch_svd_finish<double>(const SvdSec*, int, const double*, double*, int*, cudaStream_t);
+template void launch_svd_finish<float>(const SvdSec*, int, const float*, double*, int*, cudaStream_t);
 
 void launch_truncate(const SvdSec* secs, int nsec, const double* sig, const int* order, int total, int m_max,
-                     double rel_cutoff, double degen_tol, int* kept, double* weights, cudaStream_t st) {
+                     double rel_cutoff, double degen_tol, int* kept, double* weights, double* scratch_d, int* scratch_i,
+                     cudaStream_t st) {
     PD_REQUIRE(nsec <= 256, DMRG_ERR_CAPACITY, "more than 256 charge sectors on one bond");
-    PD_REQUIRE(total <= 10000, DMRG_ERR_CAPACITY, "more than 10000 singular values on one bond");
-    size_t smem = (size_t)total * (sizeof(double) + 3 * sizeof(int)) + 16;
-    if (smem > 48 * 1024)
-        PD_CK(cudaFuncSetAttribute(k_truncate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_truncate<<<1, 1024, smem, st>>>(secs, nsec, sig, order, total, m_max, rel_cutoff, degen_tol, kept, weights);
+    if (total <= 0) return;
+    double* lam = scratch_d;
+    double* lmax = scratch_d + total;
+    int* sec = scratch_i;
+    int* pos = scratch_i + total;
+    int* rank = scratch_i + 2 * total;
+    k_trunc_flat<<<nsec, 256, 0, st>>>(secs, nsec, sig, order, lam, sec, pos, lmax);
+    PD_LAUNCHED();
+    k_trunc_rank<<<(total + 127) / 128, 128, 0, st>>>(lam, sec, pos, total, lmax, nsec, rel_cutoff, rank);
+    PD_LAUNCHED();
+    k_trunc_count<<<1, 1024, 0, st>>>(lam, sec, rank, total, nsec, m_max, degen_tol, kept, weights);
     PD_LAUNCHED();
 }
 

@@ -128,18 +128,27 @@ void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaS
     if (g.empty()) return;
     g.upload_tiles(64, 64, st);
     void* tok = prof_on() ? prof_start(st) : nullptr;
-    launch_gemm64(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);
+    launch_gemm_simt<double>(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);
     if (tok) prof_stop(tok, st, PROF_F64, g.flops);
+}
+
+void run_gemm32(GemmBatch& g, const float* A, const float* B, float* C, cudaStream_t st) {
+    if (g.empty()) return;
+    g.upload_tiles(64, 64, st);
+    void* tok = prof_on() ? prof_start(st) : nullptr;
+    launch_gemm_simt<float>(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);
+    if (tok) prof_stop(tok, st, PROF_F32, g.flops);
 }
 
 template <class Tin>
 void run_copy(const CopyList& c, const Tin* src, void* dst, Num out, cudaStream_t st) {
     if (c.jobs.empty()) return;
     const CopyJob* j = c.d.as<CopyJob>();
-    int n = (int)c.jobs.size();
-    if (out == Num::F64) launch_copy<Tin, double>(j, n, c.max_elems, src, (double*)dst, st);
-    else if (out == Num::F32) launch_copy<Tin, float>(j, n, c.max_elems, src, (float*)dst, st);
-    else launch_copy<Tin, __nv_bfloat16>(j, n, c.max_elems, src, (__nv_bfloat16*)dst, st);
+    const int2* ch = c.dc.as<int2>();
+    int n = c.nchunks;
+    if (out == Num::F64) launch_copy<Tin, double>(j, ch, n, src, (double*)dst, st);
+    else if (out == Num::F32) launch_copy<Tin, float>(j, ch, n, src, (float*)dst, st);
+    else launch_copy<Tin, __nv_bfloat16>(j, ch, n, src, (__nv_bfloat16*)dst, st);
 }
 template void run_copy<double>(const CopyList&, const double*, void*, Num, cudaStream_t);
 template void run_copy<float>(const CopyList&, const float*, void*, Num, cudaStream_t);
@@ -148,15 +157,15 @@ template <>
 void run_mix<double>(const MixList& m, const double* in, void* out, Num t, cudaStream_t st) {
     if (m.jobs.empty()) return;
     PD_REQUIRE(t == Num::F64, DMRG_ERR_ARG, "FP64 mix output must be FP64");
-    launch_mix<double, double>(m.dj.as<MixJob>(), (int)m.jobs.size(), m.max_elems, m.dt.as<MixTerm>(), in, (double*)out, st);
+    launch_mix<double, double>(m.dj.as<MixJob>(), m.dc.as<int2>(), m.nchunks, m.dt.as<MixTerm>(), in, (double*)out, st);
 }
 template <>
 void run_mix<float>(const MixList& m, const float* in, void* out, Num t, cudaStream_t st) {
     if (m.jobs.empty()) return;
     if (t == Num::F32)
-        launch_mix<float, float>(m.dj.as<MixJob>(), (int)m.jobs.size(), m.max_elems, m.dt.as<MixTerm>(), in, (float*)out, st);
+        launch_mix<float, float>(m.dj.as<MixJob>(), m.dc.as<int2>(), m.nchunks, m.dt.as<MixTerm>(), in, (float*)out, st);
     else
-        launch_mix<float, __nv_bfloat16>(m.dj.as<MixJob>(), (int)m.jobs.size(), m.max_elems, m.dt.as<MixTerm>(), in, (__nv_bfloat16*)out, st);
+        launch_mix<float, __nv_bfloat16>(m.dj.as<MixJob>(), m.dc.as<int2>(), m.nchunks, m.dt.as<MixTerm>(), in, (__nv_bfloat16*)out, st);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -193,7 +202,8 @@ struct ScatJob {
     int lam_pow;         // multiply by lambda_t (normalised) when 1
     int pad_;
 };
-__global__ void k_svd_scatter(const ScatJob* jobs, const double* W, const double* V, const double* sig,
+template <class T>
+__global__ void k_svd_scatter(const ScatJob* jobs, const T* W, const T* V, const double* sig,
                               const int* order, const double* weights, double* out) {
     const ScatJob j = jobs[blockIdx.y];
     const double nrm = sqrt(weights[1]);
@@ -204,8 +214,8 @@ __global__ void k_svd_scatter(const ScatJob* jobs, const double* W, const double
         int x = j.left ? r : c;          // position inside the source column
         int col = order[j.s_off + t];
         double sg = sig[j.s_off + col];
-        double val = j.fromW ? W[j.base + (long long)col * j.ld + j.off0 + x] / sg
-                             : V[j.base + (long long)col * j.ld + j.off0 + x];
+        double val = j.fromW ? (double)W[j.base + (long long)col * j.ld + j.off0 + x] / sg
+                             : (double)V[j.base + (long long)col * j.ld + j.off0 + x];
         if (j.lam_pow) val *= sg / nrm;
         out[j.dst + e] = val;
     }
@@ -266,6 +276,118 @@ void scale_site(const Sec& bl, const Sec& br, const std::vector<int>& qn, const 
     upload(dj, jobs, st);
     k_rcscale<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<RCJob>(), in, lam, out);
     PD_LAUNCHED();
+    PD_CK(cudaStreamSynchronize(st));
+}
+
+namespace {
+// T_j = 1.5 I - 0.5 G_j for square blocks (off, k)
+struct NsJob { long long off; int k, pad_; };
+__global__ void k_ns_prep(const NsJob* jobs, const double* G, double* T) {
+    const NsJob j = jobs[blockIdx.y];
+    long long total = (long long)j.k * j.k;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e / j.k), c = (int)(e % j.k);
+        T[j.off + e] = (r == c ? 1.5 : 0.0) - 0.5 * G[j.off + e];
+    }
+}
+}  // namespace
+
+namespace {
+// max over sectors of |G - I|_max, written by one block per sector into dev[s]
+struct DevJob { long long off; int k, pad_; };
+__global__ void k_gram_dev(const DevJob* jobs, const double* G, double* dev) {
+    const DevJob j = jobs[blockIdx.x];
+    double m = 0.0;
+    const long long total = (long long)j.k * j.k;
+    for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+        int r = (int)(e / j.k), c = (int)(e % j.k);
+        m = fmax(m, fabs(G[j.off + e] - (r == c ? 1.0 : 0.0)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
+        dev[blockIdx.x] = x;
+    }
+}
+}  // namespace
+
+void orthonormalize_factor(const Sec& bl, const Sec& br, const std::vector<int>& qn, double* X, bool left,
+                           cudaStream_t st) {
+    const SiteLayout S = site_layout(bl, br, qn);
+    const Sec& mid = left ? br : bl;            // the bond carrying the kept index
+    std::vector<long long> goff(mid.n() + 1, 0);
+    for (int i = 0; i < mid.n(); ++i) goff[i + 1] = goff[i] + (long long)mid.m[i] * mid.m[i];
+    DBuf G, T, out, dev, dj, djd;
+    G.ensure(std::max<long long>(1, goff.back()) * 8, st);
+    T.ensure(std::max<long long>(1, goff.back()) * 8, st);
+    out.ensure(std::max<long long>(1, S.size) * 8, st);
+    dev.ensure(std::max(1, mid.n()) * 8, st);
+    std::vector<NsJob> jobs;
+    std::vector<DevJob> djobs;
+    int mx = 1;
+    for (int j = 0; j < mid.n(); ++j) {
+        jobs.push_back({goff[j], mid.m[j], 0});
+        djobs.push_back({goff[j], mid.m[j], 0});
+        mx = std::max(mx, mid.m[j] * mid.m[j]);
+    }
+    upload(dj, jobs, st);
+    upload(djd, djobs, st);
+    GemmBatch gA;
+    for (const auto& b : S.blk) {
+        if (left) {
+            int k = b.cols;   // A'[a][t] = sum_u A[a][u] T[u][t]:  C(m = t, n = a)
+            gA.add(k, b.rows, b.off, 1, k, k, 1, 1, k, {GSeg{goff[b.j], b.off, k, 0}});
+        } else {
+            int k = b.rows;   // B'[t][c] = sum_u T[t][u] B[u][c]:  C(m = c, n = t)
+            gA.add(b.cols, k, b.off, 1, b.cols, k, 1, 1, b.cols, {GSeg{b.off, goff[b.i], k, 0}});
+        }
+    }
+    GemmBatch gG;
+    std::vector<GemmBatch> per_block;
+    if (left) {
+        // G_j = sum over the blocks (a, s) of sector j of A^T A; all blocks share k_j columns
+        std::vector<std::vector<GSeg>> segs(mid.n());
+        for (const auto& b : S.blk) segs[b.j].push_back({b.off, b.off, b.rows, 0});
+        for (int j = 0; j < mid.n(); ++j) gG.add(mid.m[j], mid.m[j], goff[j], 1, mid.m[j], 1, mid.m[j], 1, mid.m[j], segs[j]);
+    } else {
+        // G_j = sum over the blocks of B B^T; row strides differ per block, so one accumulating
+        // launch per block (stream order serialises them)
+        std::vector<int> first(mid.n(), 1);
+        for (const auto& b : S.blk) {
+            per_block.emplace_back();
+            int k = b.rows;
+            per_block.back().add(k, k, goff[b.i], b.cols, 1, b.cols, 1, 1, k, {GSeg{b.off, b.off, b.cols, 0}},
+                                 first[b.i] ? 0 : 1);
+            first[b.i] = 0;
+        }
+    }
+    std::vector<double> hdev(mid.n());
+    for (int iter = 0; iter < 6; ++iter) {
+        PD_CK(cudaMemsetAsync(G.p, 0, std::max<long long>(1, goff.back()) * 8, st));
+        if (left) run_gemm64(gG, X, X, G.as<double>(), st);
+        else
+            for (auto& g1 : per_block) run_gemm64(g1, X, X, G.as<double>(), st);
+        k_gram_dev<<<mid.n(), 256, 0, st>>>(djd.as<DevJob>(), G.as<double>(), dev.as<double>());
+        PD_LAUNCHED();
+        PD_CK(cudaMemcpyAsync(hdev.data(), dev.p, mid.n() * 8, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+        double worst = 0.0;
+        for (double v : hdev) worst = std::max(worst, v);
+        PD_REQUIRE(std::isfinite(worst) && worst < 0.9, DMRG_ERR_NUMERIC,
+                   "kept singular vectors too far from orthonormal for the FP64 re-orthonormalisation");
+        if (worst < 1e-13 || iter == 5) break;
+        // X <- X (3I - G)/2 (left) or (3I - G)/2 X (right): one Newton-Schulz step
+        k_ns_prep<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<NsJob>(), G.as<double>(),
+                                                                               T.as<double>());
+        PD_LAUNCHED();
+        if (left) run_gemm64(gA, T.as<double>(), X, out.as<double>(), st);
+        else run_gemm64(gA, X, T.as<double>(), out.as<double>(), st);
+        PD_CK(cudaMemcpyAsync(X, out.p, S.size * 8, cudaMemcpyDeviceToDevice, st));
+    }
     PD_CK(cudaStreamSynchronize(st));
 }
 
@@ -413,10 +535,18 @@ std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std
     P->mix.up(st);
     upload(P->ddj, P->djobs, st);
     upload(P->ddt, P->dterms, st);
+    {
+        std::vector<long long> el;
+        for (const auto& j : P->djobs) el.push_back((long long)j.rows * j.cols);
+        std::vector<int2> c = make_chunks(el);
+        P->diag_chunks = (int)c.size();
+        upload(P->ddc, c, st);
+    }
     const Num t = mv_num(prec);
     P->psiT.ensure(std::max<long long>(1, P->psiT_rows) * P->ld_psi * num_size(t), st);
     P->Y.ensure(std::max<long long>(1, P->y_rows) * P->ld_y * num_size(t), st);
     P->X.ensure(std::max<long long>(1, P->x_size) * (prec == DMRG_FP64 ? 8 : 4), st);
+    PD_REQUIRE(P->psi.size < (1LL << 31), DMRG_ERR_CAPACITY, "two-site vector too long for one copy job");
     return P;
 }
 
@@ -439,6 +569,22 @@ void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x
         run_gemm64(P.lstage, P.psiT.as<double>(), L.buf.as<double>(), P.X.as<double>(), st);
         run_mix<double>(P.mix, P.X.as<double>(), P.Y.p, Num::F64, st);
         run_gemm64(P.rstage, R.buf.as<double>(), P.Y.as<double>(), y, st);
+    } else if (prec == PREC_F32) {
+        // accurate refinement matvec: FP32 everywhere, FP64 output
+        DBuf y32;
+        y32.ensure(std::max<long long>(1, P.psi.size) * 4, st);
+        PD_CK(cudaMemsetAsync(y32.p, 0, std::max<long long>(1, P.psi.size) * 4, st));
+        run_gemm32(P.lstage, P.psiT.as<float>(), L.buf.as<float>(), P.X.as<float>(), st);
+        run_mix<float>(P.mix, P.X.as<float>(), P.Y.p, Num::F32, st);
+        run_gemm32(P.rstage, R.buf.as<float>(), P.Y.as<float>(), y32.as<float>(), st);
+        if (!P.unpack.d.p) {
+            CopyJob j{};
+            j.src = 0; j.dst = 0; j.rows = 1; j.cols = (int)P.psi.size; j.srs = 0; j.scs = 1; j.drs = 0; j.dcs = 1;
+            j.zero_to = 0; j.scale = 1.0;
+            P.unpack.add(j);
+            P.unpack.up(st);
+        }
+        run_copy<float>(P.unpack, y32.as<float>(), y, Num::F64, st);
     } else {
         run_gemm_tc(P.lstage, t, P.psiT.p, P.psiT_rows, P.ld_psi, env_operand(L, prec), L.lay.rows, L.lay.ld,
                     P.X.p, false, err, st);
@@ -450,10 +596,10 @@ void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x
 void heff_diag(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* out, cudaStream_t st) {
     if (P.djobs.empty()) return;
     if (L.num == Num::F64)
-        launch_diag<double>(P.ddj.as<DiagJob>(), (int)P.djobs.size(), P.diag_max, P.ddt.as<DiagTerm>(),
+        launch_diag<double>(P.ddj.as<DiagJob>(), P.ddc.as<int2>(), P.diag_chunks, P.ddt.as<DiagTerm>(),
                             L.buf.as<double>(), L.lay.ld, R.buf.as<double>(), R.lay.ld, out, st);
     else
-        launch_diag<float>(P.ddj.as<DiagJob>(), (int)P.djobs.size(), P.diag_max, P.ddt.as<DiagTerm>(),
+        launch_diag<float>(P.ddj.as<DiagJob>(), P.ddc.as<int2>(), P.diag_chunks, P.ddt.as<DiagTerm>(),
                            L.buf.as<float>(), L.lay.ld, R.buf.as<float>(), R.lay.ld, out, st);
 }
 
@@ -534,11 +680,14 @@ void env_boundary(EnvSlab& e, const Sec& b, const std::vector<int>& flux, int pr
 // ------------------------------------------------------------------------------------------
 // Environment updates (Sec. II operator transformation)
 // ------------------------------------------------------------------------------------------
+// Environment updates compound their rounding errors site after site, so they run at FP32
+// accuracy or better in every mode (FP64 SIMT in FP64 mode, FP32 SIMT in the mixed modes).
 static void run_env_gemm(GemmBatch& g, int prec, const void* A, long long arows, int lda, const void* B,
                          long long brows, int ldb, void* C, unsigned* err, cudaStream_t st) {
+    (void)arows; (void)lda; (void)brows; (void)ldb; (void)err;
     if (g.empty()) return;
     if (prec == DMRG_FP64) run_gemm64(g, (const double*)A, (const double*)B, (double*)C, st);
-    else run_gemm_tc(g, Num::F32, A, arows, lda, B, brows, ldb, C, false, err, st);
+    else run_gemm32(g, (const float*)A, (const float*)B, (float*)C, st);
 }
 
 void env_update_left(const Sec& ba, const Sec& bb, const std::vector<int>& qn, const SiteMPO& W,
@@ -856,8 +1005,10 @@ void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
 
 SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
                       const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
-                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st) {
+                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st,
+                      bool fp32) {
     (void)accurate;
+    const size_t es = fp32 ? 4 : 8;
     const PsiLayout P = psi_layout2(bl, br, qn1, qn2);
     const std::vector<int>& qn = qn1;
     // sector layout: rows (i, s1) sorted, cols (s2, k) sorted, per middle charge
@@ -903,35 +1054,63 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         }
         gather.add(j);
     }
-    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts;
-    dW.ensure(std::max<long long>(1, woff) * 8, st);
-    dV.ensure(std::max<long long>(1, voff) * 8, st);
+    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dfloor;
+    const int max_sweeps = 60;
+    dfloor.ensure(std::max(1, nsec) * 8, st);
+    dW.ensure(std::max<long long>(1, woff) * es, st);
+    dV.ensure(std::max<long long>(1, voff) * es, st);
     dsig.ensure(std::max<long long>(1, soff) * 8, st);
     dord.ensure(std::max<long long>(1, soff) * 4, st);
     dkept.ensure(std::max(1, nsec) * 4, st);
     dwts.ensure(16, st);
-    drot.ensure(4, st);
+    drot.ensure((max_sweeps + 1) * 4, st);
     upload(dsecs, ss, st);
     upload(dpairs, pair_sec, st);
     gather.up(st);
-    PD_CK(cudaMemsetAsync(dW.p, 0, std::max<long long>(1, woff) * 8, st));
-    run_copy<double>(gather, psi, dW.p, Num::F64, st);
-    launch_svd_init_v(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
-    const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+    PD_CK(cudaMemsetAsync(dW.p, 0, std::max<long long>(1, woff) * es, st));
+    PD_CK(cudaMemsetAsync(drot.p, 0, (max_sweeps + 1) * 4, st));
     const int npairs = (int)pair_sec.size();
-    for (int sweep = 0; sweep < 80; ++sweep) {
-        PD_CK(cudaMemsetAsync(drot.p, 0, 4, st));
-        for (int round = 0; round < maxnpad - 1; ++round)
-            launch_jacobi_round(dsecs.as<SvdSec>(), dpairs.as<int>(), npairs, round, dW.as<double>(),
-                                dV.as<double>(), tol, drot.as<int>(), st);
-        int rot = 0;
-        PD_CK(cudaMemcpyAsync(&rot, drot.p, 4, cudaMemcpyDeviceToHost, st));
-        PD_CK(cudaStreamSynchronize(st));
-        if (!rot) break;
+    cudaEvent_t sv0 = nullptr, sv1 = nullptr;
+    if (prof_on()) {
+        PD_CK(cudaEventCreate(&sv0));
+        PD_CK(cudaEventCreate(&sv1));
+        PD_CK(cudaEventRecord(sv0, st));
     }
-    launch_svd_finish(dsecs.as<SvdSec>(), nsec, maxn, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
+    if (fp32) {
+        run_copy<double>(gather, psi, dW.p, Num::F32, st);
+        launch_svd_init_v<float>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<float>(), st);
+        // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it; the
+        // kept factor that joins a block is re-orthonormalised in FP64 afterwards
+        const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)maxp));
+        launch_jacobi<float>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, 40, dW.as<float>(),
+                             dV.as<float>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(), drot.as<int>() + max_sweeps,
+                             st);
+        launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
+    } else {
+        run_copy<double>(gather, psi, dW.p, Num::F64, st);
+        launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
+        const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+        launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps,
+                              dW.as<double>(), dV.as<double>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(),
+                              drot.as<int>() + max_sweeps, st);
+        launch_svd_finish<double>(dsecs.as<SvdSec>(), nsec, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
+    }
+    if (sv0) {
+        PD_CK(cudaEventRecord(sv1, st));
+        int sweeps = 0;
+        PD_CK(cudaMemcpyAsync(&sweeps, drot.as<int>() + max_sweeps, 4, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        PD_CK(cudaEventElapsedTime(&ms, sv0, sv1));
+        prof_svd(sweeps, ms);
+        cudaEventDestroy(sv0);
+        cudaEventDestroy(sv1);
+    }
+    DBuf tsd, tsi;
+    tsd.ensure((size_t)(total + nsec + 1) * 8, st);
+    tsi.ensure((size_t)(3 * total + 1) * 4, st);
     launch_truncate(dsecs.as<SvdSec>(), nsec, dsig.as<double>(), dord.as<int>(), total, m_max, rel_cutoff, 1e-10,
-                    dkept.as<int>(), dwts.as<double>(), st);
+                    dkept.as<int>(), dwts.as<double>(), tsd.as<double>(), tsi.as<int>(), st);
     std::vector<int> kept(nsec);
     double wts[2];
     PD_CK(cudaMemcpyAsync(kept.data(), dkept.p, 4 * nsec, cudaMemcpyDeviceToHost, st));
@@ -987,16 +1166,19 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     DBuf dja, djb;
     upload(dja, ja, st);
     upload(djb, jb, st);
-    if (!ja.empty()) {
-        k_svd_scatter<<<dim3(gridn(mx, 256), (unsigned)ja.size()), 256, 0, st>>>(
-            dja.as<ScatJob>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(), dord.as<int>(), dwts.as<double>(), A_out);
+    auto scatter = [&](const std::vector<ScatJob>& jobs_, const DBuf& dj, double* out) {
+        if (jobs_.empty()) return;
+        dim3 g(gridn(mx, 256), (unsigned)jobs_.size());
+        if (fp32)
+            k_svd_scatter<float><<<g, 256, 0, st>>>(dj.as<ScatJob>(), dW.as<float>(), dV.as<float>(), dsig.as<double>(),
+                                                    dord.as<int>(), dwts.as<double>(), out);
+        else
+            k_svd_scatter<double><<<g, 256, 0, st>>>(dj.as<ScatJob>(), dW.as<double>(), dV.as<double>(),
+                                                     dsig.as<double>(), dord.as<int>(), dwts.as<double>(), out);
         PD_LAUNCHED();
-    }
-    if (!jb.empty()) {
-        k_svd_scatter<<<dim3(gridn(mx, 256), (unsigned)jb.size()), 256, 0, st>>>(
-            djb.as<ScatJob>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(), dord.as<int>(), dwts.as<double>(), B_out);
-        PD_LAUNCHED();
-    }
+    };
+    scatter(ja, dja, A_out);
+    scatter(jb, djb, B_out);
     // lambda
     std::vector<LamJob> lj;
     long long o = 0;
@@ -1025,7 +1207,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
 // Davidson (the Sec. II local eigensolver), FP64 vectors, same algorithm as the CPU oracle
 // ------------------------------------------------------------------------------------------
 DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, int kmax, double tol,
-                   int max_iter, unsigned* err, cudaStream_t st) {
+                   int max_iter, unsigned* err, cudaStream_t st, HeffPlan* acc, int refine_iters) {
     const long long n = P.psi.size;
     PD_REQUIRE(kmax >= 2 && kmax <= 32, DMRG_ERR_ARG, "Davidson kmax must be in [2, 32]");
     DavResult res;
@@ -1050,70 +1232,84 @@ DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, i
     cudaEvent_t e0, e1;
     PD_CK(cudaEventCreate(&e0));
     PD_CK(cudaEventCreate(&e1));
+    HeffPlan* cur = &P;
     auto mv = [&](const double* in, double* out) {
         PD_CK(cudaEventRecord(e0, st));
-        heff_apply(P, L, R, in, out, err, st);
+        heff_apply(*cur, L, R, in, out, err, st);
         PD_CK(cudaEventRecord(e1, st));
         PD_CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         PD_CK(cudaEventElapsedTime(&ms, e0, e1));
-        res.mv_ms += ms;
-        res.matvecs++;
+        if (cur == &P) {
+            res.mv_ms += ms;
+            res.matvecs++;
+        } else {
+            res.acc_ms += ms;
+            res.acc_matvecs++;
+        }
     };
     heff_diag(P, L, R, ddg.as<double>(), st);
-    // V0 = x / |x|
-    launch_nrm2(x, n, dpart.as<double>(), nch, dnrm.as<double>(), st);
-    launch_scale(x, dnrm.as<double>(), n, V, 1, st);
-    mv(V, AV);
-    int k = 1;
-    launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
-    k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
-    PD_LAUNCHED();
     double hn[4];
-    for (int it = 1; it <= max_iter; ++it) {
-        res.iters = it;
-        launch_small_eig(G, k, kmax, dyth.as<double>(), st);
-        launch_ritz(V, AV, n, k, dyth.as<double>(), n, du.as<double>(), dAu.as<double>(), dr.as<double>(),
-                    dpart.as<double>(), nch, dnrm.as<double>(), st);
-        PD_CK(cudaMemcpyAsync(hn, dnrm.p, 16, cudaMemcpyDeviceToHost, st));
-        PD_CK(cudaMemcpyAsync(hn + 2, dyth.p, 8, cudaMemcpyDeviceToHost, st));
-        PD_CK(cudaStreamSynchronize(st));
-        res.theta = hn[2];
-        res.rnorm = std::sqrt(std::max(0.0, hn[0]));
-        PD_REQUIRE(std::isfinite(res.theta) && std::isfinite(res.rnorm), DMRG_ERR_NUMERIC,
-                   "non-finite Ritz value in Davidson");
-        if (res.rnorm <= tol * std::max(1.0, std::fabs(res.theta)) || it == max_iter) break;
-        launch_precond(dr.as<double>(), ddg.as<double>(), dyth.as<double>(), 1e-4, n, dt.as<double>(), st);
-        if (k >= kmax) {   // restart from the Ritz vector
-            launch_scale(du.as<double>(), dnrm.as<double>() + 1, n, V, 1, st);
-            launch_scale(dAu.as<double>(), dnrm.as<double>() + 1, n, AV, 1, st);
-            k = 1;
-            launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
-            k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
-            PD_LAUNCHED();
-        }
-        for (int pass = 0; pass < 2; ++pass) {
-            launch_dots(V, n, k, dt.as<double>(), n, dpart.as<double>(), nch, dd1.as<double>(), st);
-            launch_subtract(V, n, k, dd1.as<double>(), n, dt.as<double>(), st);
-        }
-        launch_nrm2(dt.as<double>(), n, dpart.as<double>(), nch, dnrm.as<double>() + 2, st);
-        double tn2 = 0.0;
-        PD_CK(cudaMemcpyAsync(&tn2, dnrm.as<double>() + 2, 8, cudaMemcpyDeviceToHost, st));
-        PD_CK(cudaStreamSynchronize(st));
-        if (std::sqrt(tn2) < 1e-14) break;
-        double* vk = V + (size_t)k * n;
-        double* avk = AV + (size_t)k * n;
-        launch_scale(dt.as<double>(), dnrm.as<double>() + 2, n, vk, 1, st);
-        mv(vk, avk);
-        // new column k: G[i][k] = V_i . AV_k (i <= k); new row: G[k][i] = V_k . AV_i (i < k)
-        launch_dots(V, n, k + 1, avk, n, dpart.as<double>(), nch, dd1.as<double>(), st);
-        launch_dots(AV, n, k, vk, n, dpart.as<double>(), nch, dd2.as<double>(), st);
-        k_place<<<1, 32, 0, st>>>(G, kmax, k, dd1.as<double>(), dd2.as<double>());
+    // one Davidson run from the normalised vector in x; leaves the Ritz vector in du (|u|^2 in dnrm[1])
+    auto run = [&](int iters) {
+        launch_nrm2(x, n, dpart.as<double>(), nch, dnrm.as<double>(), st);
+        launch_scale(x, dnrm.as<double>(), n, V, 1, st);
+        mv(V, AV);
+        int k = 1;
+        launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
+        k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
         PD_LAUNCHED();
-        ++k;
+        for (int it = 1; it <= iters; ++it) {
+            res.iters++;
+            launch_small_eig(G, k, kmax, dyth.as<double>(), st);
+            launch_ritz(V, AV, n, k, dyth.as<double>(), n, du.as<double>(), dAu.as<double>(), dr.as<double>(),
+                        dpart.as<double>(), nch, dnrm.as<double>(), st);
+            PD_CK(cudaMemcpyAsync(hn, dnrm.p, 16, cudaMemcpyDeviceToHost, st));
+            PD_CK(cudaMemcpyAsync(hn + 2, dyth.p, 8, cudaMemcpyDeviceToHost, st));
+            PD_CK(cudaStreamSynchronize(st));
+            res.theta = hn[2];
+            res.rnorm = std::sqrt(std::max(0.0, hn[0]));
+            PD_REQUIRE(std::isfinite(res.theta) && std::isfinite(res.rnorm), DMRG_ERR_NUMERIC,
+                       "non-finite Ritz value in Davidson");
+            if (res.rnorm <= tol * std::max(1.0, std::fabs(res.theta)) || it == iters) break;
+            launch_precond(dr.as<double>(), ddg.as<double>(), dyth.as<double>(), 1e-4, n, dt.as<double>(), st);
+            if (k >= kmax) {   // restart from the Ritz vector
+                launch_scale(du.as<double>(), dnrm.as<double>() + 1, n, V, 1, st);
+                launch_scale(dAu.as<double>(), dnrm.as<double>() + 1, n, AV, 1, st);
+                k = 1;
+                launch_dots(V, n, 1, AV, n, dpart.as<double>(), nch, dd1.as<double>(), st);
+                k_place<<<1, 32, 0, st>>>(G, kmax, 0, dd1.as<double>(), dd1.as<double>());
+                PD_LAUNCHED();
+            }
+            for (int pass = 0; pass < 2; ++pass) {
+                launch_dots(V, n, k, dt.as<double>(), n, dpart.as<double>(), nch, dd1.as<double>(), st);
+                launch_subtract(V, n, k, dd1.as<double>(), n, dt.as<double>(), st);
+            }
+            launch_nrm2(dt.as<double>(), n, dpart.as<double>(), nch, dnrm.as<double>() + 2, st);
+            double tn2 = 0.0;
+            PD_CK(cudaMemcpyAsync(&tn2, dnrm.as<double>() + 2, 8, cudaMemcpyDeviceToHost, st));
+            PD_CK(cudaStreamSynchronize(st));
+            if (std::sqrt(tn2) < 1e-14) break;
+            double* vk = V + (size_t)k * n;
+            double* avk = AV + (size_t)k * n;
+            launch_scale(dt.as<double>(), dnrm.as<double>() + 2, n, vk, 1, st);
+            mv(vk, avk);
+            // new column k: G[i][k] = V_i . AV_k (i <= k); new row: G[k][i] = V_k . AV_i (i < k)
+            launch_dots(V, n, k + 1, avk, n, dpart.as<double>(), nch, dd1.as<double>(), st);
+            launch_dots(AV, n, k, vk, n, dpart.as<double>(), nch, dd2.as<double>(), st);
+            k_place<<<1, 32, 0, st>>>(G, kmax, k, dd1.as<double>(), dd2.as<double>());
+            PD_LAUNCHED();
+            ++k;
+        }
+        // x = u / |u|
+        launch_scale(du.as<double>(), dnrm.as<double>() + 1, n, x, 1, st);
+    };
+    run(max_iter);
+    if (acc && refine_iters > 0) {
+        PD_REQUIRE(acc->psi.size == n, DMRG_ERR_STATE, "refinement plan does not match the bond");
+        cur = acc;
+        run(refine_iters);
     }
-    // x = u / |u|
-    launch_scale(du.as<double>(), dnrm.as<double>() + 1, n, x, 1, st);
     PD_CK(cudaStreamSynchronize(st));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

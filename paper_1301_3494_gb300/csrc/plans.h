@@ -125,6 +125,9 @@ EnvLayout env_layout(const Sec& b, const std::vector<int>& flux, int ld);
 // Element type used for the tensor-core operand slabs and the row padding they need.
 enum class Num { F64, F32, BF16 };
 inline size_t num_size(Num t) { return t == Num::F64 ? 8 : (t == Num::F32 ? 4 : 2); }
+// Internal matvec arithmetic for the accurate Davidson refinement of the mixed modes: FP32
+// operands and accumulation on the CUDA cores (same slab layout as TF32).
+constexpr int PREC_F32 = 3;
 inline int pad_ld(int x, int prec) {
     int a = (prec == DMRG_FP64) ? 2 : 64;
     x = std::max(x, 1);
@@ -132,7 +135,9 @@ inline int pad_ld(int x, int prec) {
 }
 inline int kpad(int K, int prec) { return prec == DMRG_FP64 ? K : (K + 63) / 64 * 64; }
 // Operand types per precision: matvec operands / environment-update operands / env storage.
-inline Num mv_num(int prec) { return prec == DMRG_FP64 ? Num::F64 : (prec == DMRG_TF32 ? Num::F32 : Num::BF16); }
+inline Num mv_num(int prec) {
+    return prec == DMRG_FP64 ? Num::F64 : ((prec == DMRG_TF32 || prec == PREC_F32) ? Num::F32 : Num::BF16);
+}
 inline Num env_num(int prec) { return prec == DMRG_FP64 ? Num::F64 : Num::F32; }
 
 // ------------------------------------------------------------------------------------------
@@ -170,6 +175,7 @@ struct GemmBatch {
 // Run a batch: FP64 SIMT (A, B, C double) or tensor core (A, B slabs of type `t`, C of type
 // float or double per `c_is_f64`).
 void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st);
+void run_gemm32(GemmBatch& g, const float* A, const float* B, float* C, cudaStream_t st);
 void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B,
                  long long b_rows, int ldb, void* C, bool c_is_f64, unsigned* err, cudaStream_t st);
 bool tc_available();
@@ -179,21 +185,38 @@ bool tc_available();
 // ------------------------------------------------------------------------------------------
 struct CopyList {
     std::vector<CopyJob> jobs;
-    DBuf d;
+    std::vector<long long> elems;
+    DBuf d, dc;
+    int nchunks = 0;
     int max_elems = 0;
     void add(const CopyJob& j) {
         jobs.push_back(j);
+        elems.push_back((long long)j.rows * std::max(j.cols, j.zero_to));
         max_elems = std::max(max_elems, j.rows * std::max(j.cols, j.zero_to));
     }
-    void up(cudaStream_t st) { upload(d, jobs, st); }
+    void up(cudaStream_t st) {
+        upload(d, jobs, st);
+        std::vector<int2> c = make_chunks(elems);
+        nchunks = (int)c.size();
+        upload(dc, c, st);
+    }
 };
 struct MixList {
     std::vector<MixJob> jobs;
     std::vector<MixTerm> terms;
-    DBuf dj, dt;
+    DBuf dj, dt, dc;
+    int nchunks = 0;
     int max_elems = 0;
     double flops = 0.0;
-    void up(cudaStream_t st) { upload(dj, jobs, st); upload(dt, terms, st); }
+    void up(cudaStream_t st) {
+        upload(dj, jobs, st);
+        upload(dt, terms, st);
+        std::vector<long long> el;
+        for (const auto& j : jobs) el.push_back((long long)j.rows * std::max(j.cols, j.zero_to));
+        std::vector<int2> c = make_chunks(el);
+        nchunks = (int)c.size();
+        upload(dc, c, st);
+    }
 };
 
 template <class Tin>
@@ -236,12 +259,13 @@ struct HeffPlan {
     int ld_psi = 0, ld_y = 0;
     long long psiT_rows = 0, y_rows = 0, x_size = 0;
     CopyList pack;            // canonical x -> psiT slab
+    CopyList unpack;          // FP32 result -> FP64 (accurate refinement plan)
     GemmBatch lstage, rstage;
     MixList mix;              // X -> Y slab
     std::vector<DiagJob> djobs;
     std::vector<DiagTerm> dterms;
-    DBuf ddj, ddt;
-    int diag_max = 0;
+    DBuf ddj, ddt, ddc;
+    int diag_max = 0, diag_chunks = 0;
     double flops = 0.0;
     // scratch
     DBuf psiT, X, Y;
@@ -285,7 +309,13 @@ struct SplitResult {
 // lam_pow_left/right: 0 or 1 -> A (left factor) multiplied by Lambda^pow_left, B by Lambda^pow_right.
 SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
                       const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
-                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st);
+                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st,
+                      bool fp32 = false);
+// FP64 re-orthonormalisation of the kept factor after a reduced-precision SVD: one Newton-Schulz
+// step per middle sector, X <- X (3I - X^T X)/2 for a left factor (blocks bl x br, kept index on
+// br), X <- (3I - X X^T)/2 X for a right factor (kept index on bl).
+void orthonormalize_factor(const Sec& bl, const Sec& br, const std::vector<int>& qn, double* X, bool left,
+                           cudaStream_t st);
 // Worst-case (untruncated) element counts of the split's A and B outputs.
 void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
                       long long* a_elems, long long* b_elems, long long* lam_elems);
@@ -293,11 +323,13 @@ void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
 // Davidson on the projected Hamiltonian (FP64 vectors).
 struct DavResult {
     double theta = 0.0, rnorm = 0.0;
-    int iters = 0, matvecs = 0;
-    float mv_ms = 0.0f;
+    int iters = 0, matvecs = 0, acc_matvecs = 0;
+    float mv_ms = 0.0f, acc_ms = 0.0f;
 };
+// Davidson with the plan's matvec; with `acc` (mixed modes) the run continues, restarted from the
+// Ritz vector, for up to refine_iters iterations with the accurate matvec of `acc`.
 DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, int kmax, double tol,
-                   int max_iter, unsigned* err, cudaStream_t st);
+                   int max_iter, unsigned* err, cudaStream_t st, HeffPlan* acc = nullptr, int refine_iters = 0);
 
 // Scale the blocks of a packed site tensor (bonds bl x br) by a per-sector vector `lam` of
 // the right bond (right_index = true: out[a][t] = in[a][t] lam[t]) or of the left bond

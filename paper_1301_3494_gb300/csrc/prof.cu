@@ -18,8 +18,10 @@ struct Rec {
 std::mutex g_mu;
 std::atomic<bool> g_on{false};
 std::vector<Rec> g_pending;
-double g_ms[3] = {0, 0, 0}, g_fl[3] = {0, 0, 0};
-long long g_n[3] = {0, 0, 0};
+long long g_svd_calls = 0, g_svd_sweeps = 0;
+double g_svd_ms = 0.0;
+double g_ms[4] = {0, 0, 0, 0}, g_fl[4] = {0, 0, 0, 0};
+long long g_n[4] = {0, 0, 0, 0};
 }  // namespace
 
 bool prof_on() { return g_on.load(std::memory_order_relaxed); }
@@ -40,6 +42,13 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops) {
     delete[] ev;
 }
 
+void prof_svd(int sweeps, double ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_svd_calls += 1;
+    g_svd_sweeps += sweeps;
+    g_svd_ms += ms;
+}
+
 }  // namespace pd
 
 using namespace pd;
@@ -56,7 +65,9 @@ void dmrg_profile_reset(void) {
         cudaEventDestroy(r.b);
     }
     g_pending.clear();
-    for (int i = 0; i < 3; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
+    for (int i = 0; i < 4; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
+    g_svd_calls = g_svd_sweeps = 0;
+    g_svd_ms = 0.0;
     g_launches.store(0);
 }
 
@@ -85,6 +96,12 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->f64_gemm_launches = g_n[PROF_F64];
     out->f64_gemm_ms = g_ms[PROF_F64];
     out->f64_gemm_flops = g_fl[PROF_F64];
+    out->f32_gemm_launches = g_n[PROF_F32];
+    out->f32_gemm_ms = g_ms[PROF_F32];
+    out->f32_gemm_flops = g_fl[PROF_F32];
+    out->svd_calls = g_svd_calls;
+    out->svd_sweeps = g_svd_sweeps;
+    out->svd_ms = g_svd_ms;
     return DMRG_OK;
 }
 

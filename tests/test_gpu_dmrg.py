@@ -106,3 +106,23 @@ def test_regions_match_oracle(R, warm):
         fids = [x["fidelity"] for x in r["merges"]]
         assert abs(g["max_fidelity"] - max(fids)) <= 1e-7
     assert abs(g["energy"] - GOLD["heisenberg_chain_L16_Sz0"]) < 1e-7
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_mixed_precision_energy_within_1e5(prec):
+    """Mixed precision (tensor-core matvec and environments, FP32 SVD on ordinary bonds, FP64
+    Davidson small problem and orthogonalisation): the converged energy, evaluated as an FP64
+    Rayleigh quotient, agrees with the FP64 oracle to 1e-5 relative."""
+    L = 30
+    mpo = wl.heisenberg_chain(L)
+    mps = wl.random_mps(L, mpo.site.qn, 0, 16, seed=0)
+    ref = O.SerialDMRG(mpo, mps)
+    eng = engine_for(pd, mpo, precision=prec)
+    load_mps(eng, mps, list(mpo.site.qn))
+    for m in (32, 64, 64, 64):
+        r = ref.sweep(m)
+        # bf16 Ritz vectors start further from the accurate ones, so they get more refinement
+        g = eng.sweep(m, dav_tol=1e-9, dav_max_iter=12, refine_iters=3 if prec == "tf32" else 6)
+    e64 = eng.energy()
+    assert abs(e64 - r["energy"]) <= 1e-5 * abs(r["energy"]), (e64, r["energy"])
+    assert abs(g["energy"] - r["energy"]) <= 1e-4 * abs(r["energy"])

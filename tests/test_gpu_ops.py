@@ -181,5 +181,6 @@ def test_env_updates_tf32(kind, m):
     gotR = LY.unpack_env(Ro.cpu().numpy(), bl, fL)
     refL = {k: refL.get(k, np.zeros_like(gotL[k])) for k in gotL}
     refR = {k: refR.get(k, np.zeros_like(gotR[k])) for k in gotR}
-    assert _nrel(gotL, refL) <= 5e-3
-    assert _nrel(gotR, refR) <= 5e-3
+    # environment updates run at FP32 accuracy in the mixed modes
+    assert _nrel(gotL, refL) <= 1e-5
+    assert _nrel(gotR, refR) <= 1e-5
