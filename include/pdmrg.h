@@ -244,6 +244,23 @@ dmrg_status dmrg_heff_apply(const dmrg_bond_desc* bd, int prec, const double* L_
                             const double* R_dev, const double* x_dev, double* y_dev,
                             double* flops_out, void* stream);
 
+/* Same result as dmrg_heff_apply in FP64 (prec = DMRG_FP64), for callers that cannot allocate
+ * device memory -- for example code whose device allocations are all owned by an external
+ * memory manager, or a thread that must not enter the CUDA allocator.  It makes no device
+ * allocation of any kind: the scratch it needs (job lists, the L-stage intermediate and the
+ * MPO-mixed intermediate) lives in one fixed 64 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.  The paper has no
+ * counterpart of this entry point.
+ *  - Inputs/outputs and layouts as in dmrg_heff_apply (device pointers owned by the caller).
+ *  - The first call on a device, made with that device current, looks up the array's device
+ *    address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ *    capture.
+ *  - All calls share the array and leave their intermediates in it; calls whose GPU work
+ *    overlaps (different streams without ordering) race on it.
+ *  - DMRG_ERR_CAPACITY when the bond needs more than the 64 MiB of scratch. */
+dmrg_status dmrg_heff_apply_noalloc(const dmrg_bond_desc* bd, const double* L_dev, const double* R_dev,
+                                    const double* x_dev, double* y_dev, void* stream);
+
 /* Left-environment update through one site (Sec. II operator transformation by A):
  * Lout[b',w',b] = sum A[a',s,b'] Lin[a',w,a] W[w,s,s',w'] A[a,s',b].  Bonds: (nl,ql,ml) left
  * of the site, (nr,qr,mr) right of it; D0/f0 and D1/f1 the MPO bonds, W1 the site's MPO

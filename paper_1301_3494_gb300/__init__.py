@@ -112,6 +112,7 @@ def lib():
         L.dmrg_get_center.argtypes = [vp, C.c_int, _ip]
         L.dmrg_destroy.argtypes = [vp]
         L.dmrg_heff_apply.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp, _dp, vp]
+        L.dmrg_heff_apply_noalloc.argtypes = [C.POINTER(BondDesc), vp, vp, vp, vp, vp]
         L.dmrg_env_left.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
         L.dmrg_env_right.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
         L.dmrg_svd_split.argtypes = [C.POINTER(BondDesc), vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, _ip, _ip, _ip,
@@ -119,7 +120,8 @@ def lib():
         for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
                      "dmrg_profile_read", "dmrg_merge",
                      "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_destroy",
-                     "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_svd_split"):
+                     "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_env_left", "dmrg_env_right",
+                     "dmrg_svd_split"):
             getattr(L, name).restype = st
         _lib = L
     return _lib
@@ -188,6 +190,11 @@ def heff_apply(bond: Bond, prec, L_dev, R_dev, x_dev, y_dev, stream=0):
     fl = C.c_double(0.0)
     _check(lib().dmrg_heff_apply(C.byref(bond.desc), int(prec), L_dev, R_dev, x_dev, y_dev, C.byref(fl), stream))
     return fl.value
+
+
+def heff_apply_noalloc(bond: Bond, L_dev, R_dev, x_dev, y_dev, stream=0):
+    """FP64 y = H_eff x without any device allocation (scratch in a fixed in-library array)."""
+    _check(lib().dmrg_heff_apply_noalloc(C.byref(bond.desc), L_dev, R_dev, x_dev, y_dev, stream))
 
 
 def env_left(bond: Bond, prec, Lin_dev, A_dev, Lout_dev, stream=0):
