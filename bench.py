@@ -51,7 +51,47 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["steps", "op"], default="steps",
+                    help="op: repeated H_eff matvecs at one bond (random environments) -- small device "
+                         "footprint, used for profiler captures")
     return ap.parse_args()
+
+
+def op_mode(args, mpo, qn, mps, center):
+    """Repeated matvecs at the benchmark bond through dmrg_heff_apply."""
+    import torch
+    import paper_1301_3494_gb300 as pd
+    rng = np.random.default_rng(1)
+    j = center
+    bl, br = mps.bonds[j], mps.bonds[j + 2]
+    f0, f1, f2 = mpo.flux[j], mpo.flux[j + 1], mpo.flux[j + 2]
+
+    def env(bond, flux):
+        return np.concatenate([rng.standard_normal(bond[q] * bond[q - int(flux[w])])
+                               for q in bond for w in range(len(flux)) if (q - int(flux[w])) in bond])
+
+    Ld = torch.as_tensor(env(bl, f0)).cuda()
+    Rd = torch.as_tensor(env(br, f2)).cuda()
+    n = sum(bl[qa] * br[qa + qn[a] + qn[b]] for qa in bl for a in range(len(qn)) for b in range(len(qn))
+            if qa + qn[a] + qn[b] in br)
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    bond = pd.Bond(qn, bl, br, mpo.W[j], f0, f1, mpo.W[j + 1], f2)
+    prec = pd.PRECISIONS[args.precision]
+    for _ in range(args.warmup):
+        pd.heff_apply(bond, prec, Ld.data_ptr(), Rd.data_ptr(), x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fl = 0.0
+    for _ in range(args.steps):
+        fl += pd.heff_apply(bond, prec, Ld.data_ptr(), Rd.data_ptr(), x.data_ptr(), y.data_ptr())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "op", "workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}",
+                      "bond": j, "precision": args.precision, "matvec_ms_incl_plan": ms,
+                      "flops_per_matvec": fl / args.steps, "tflops_incl_plan": fl / args.steps / ms / 1e9}))
 
 
 # ------------------------------------------------------------------------------------------
@@ -258,6 +298,9 @@ def main():
     if not os.path.exists(pd.LIB_PATH):
         from paper_1301_3494_gb300 import build
         build.build()
+    if args.mode == "op":
+        op_mode(args, mpo, qn, mps, center)
+        return
     W, flux, D = wl.pack_mpo(mpo)
     eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
     data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])

@@ -277,19 +277,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int m = tl.m0 + quarter * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
             const int ncols = min(BN, p.N - tl.n0);
+            // FP32 arithmetic only (FP64 issue rate is low on this part); one conversion for FP64 output
+            const float alpha = (float)p.alpha;
+            const bool scale = alpha != 1.0f;
+            const bool accum = p.accumulate != 0;
+            OutT* crow = C + p.c_off + (long long)m * p.scm;
+            const int nlim = p.N - tl.n0;
             for (int c0 = 0; c0 < ncols; c0 += 32) {
                 uint32_t r[32];
                 tc_ld32(trow + (uint32_t)c0, r);
                 if (m < p.M) {
-                    const long long base_idx = p.c_off + (long long)m * p.scm;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int n = tl.n0 + c0 + j;
-                        if (n < p.N) {
-                            const long long idx = base_idx + (long long)n * p.scn;
-                            double v = p.alpha * (double)__uint_as_float(r[j]);
-                            if (p.accumulate) v += (double)C[idx];
-                            C[idx] = (OutT)v;
+                        const int n = c0 + j;
+                        if (n < nlim) {
+                            OutT* dst = crow + (long long)(tl.n0 + n) * p.scn;
+                            float v = __uint_as_float(r[j]);
+                            if (scale) v *= alpha;
+                            if (accum) *dst = *dst + (OutT)v;
+                            else *dst = (OutT)v;
                         }
                     }
                 }
@@ -375,14 +381,23 @@ void launch_tc(GemmBatch& g, const CUtensorMap& ma, const CUtensorMap& mb, int l
     if (tok) prof_stop(tok, st, g_prof_class, g.flops);
 }
 
-// Tile width from the batch's column sizes (fewest padded columns, ties to the wider tile).
-int pick_bn(const GemmBatch& g) {
-    long long best = -1;
+// Tile width from a cost model of the batch: padded MMA work at the tensor rate plus the
+// operand bytes every tile streams through shared memory (A: 128 rows, B: BN rows per k-block)
+// at an L2-to-SM rate.  Narrow tiles waste less padding on small blocks, wide tiles re-read
+// A less often.
+int pick_bn(const GemmBatch& g, int esize) {
+    const double flop_rate = 2.0e15, byte_rate = 2.0e13;
+    double best = -1.0;
     int bn_best = 128;
     for (int bn : {256, 128, 64}) {
-        long long cols = 0;
-        for (const auto& p : g.probs) cols += (long long)((p.N + bn - 1) / bn) * bn;
-        if (best < 0 || cols < best) { best = cols; bn_best = bn; }
+        double t = 0.0;
+        for (const auto& p : g.probs) {
+            long long kpad = 0;
+            for (int s = 0; s < p.nseg; ++s) kpad += (long long)((g.segs[p.seg0 + s].K + 63) / 64) * 64;
+            const double tiles = (double)((p.M + BM - 1) / BM) * ((p.N + bn - 1) / bn);
+            t += tiles * (2.0 * BM * bn * kpad / flop_rate + (double)kpad * (BM + bn) * esize / byte_rate);
+        }
+        if (best < 0 || t < best) { best = t; bn_best = bn; }
     }
     return bn_best;
 }
@@ -405,7 +420,7 @@ void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, 
     for (const auto& p : g.probs)
         PD_REQUIRE(p.sak == 1 && p.sbk == 1 && p.sam == lda && p.sbn == ldb && p.scm == 1, DMRG_ERR_ARG,
                    "tensor-core GEMM needs K-major slabs with uniform leading dimensions");
-    const int bn = g.tile_n ? g.tile_n : pick_bn(g);
+    const int bn = g.tile_n ? g.tile_n : pick_bn(g, (int)num_size(t));
     g.upload_tiles(BM, bn, st);
     const CUtensorMap ma = make_map(t, A, a_rows, lda, BM);
     const CUtensorMap mb = make_map(t, B, b_rows, ldb, bn);
