@@ -447,10 +447,12 @@ std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std
     std::vector<char> used((size_t)w12.D0 * d * d, 0);
     for (const auto& e : w12.nz) used[((size_t)e.w * d + e.s1p) * d + e.s2p] = 1;
 
-    // L stage: X[w, b] = L_w psi_b, X block [a_bra][c]
-    struct XB { long long off; int rows, cols, iab; };
-    std::map<std::pair<int, int>, XB> xb;   // (w, b)
-    long long xoff = 0;
+    // L stage: X[w, b] = L_w psi_b, block [a_bra][c].  X blocks that feed exactly one Y block,
+    // and that Y block has no other term, are written by the GEMM epilogue straight into the Y
+    // operand slab (coefficient as alpha); only the rest goes through X and the mixing kernel.
+    struct XB { int rows, cols, iab, lb, b; long long off; int fan; };
+    std::vector<XB> xs;
+    std::map<std::pair<int, int>, int> xidx;   // (w, b) -> X block
     for (int b = 0; b < nb; ++b) {
         const auto& B = pb[b];
         for (int w = 0; w < w12.D0; ++w) {
@@ -459,54 +461,82 @@ std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std
             if (iab < 0) continue;
             int lb = L.at(iab, w);
             if (lb < 0) continue;
-            XB x{xoff, bl.m[iab], B.cols, iab};
-            xb[{w, b}] = x;
-            GSeg sg{prow[b] * P->ld_psi, L.blk[lb].row * L.ld, B.rows, 0};
-            P->lstage.add(B.cols, bl.m[iab], xoff, P->ld_psi, 1, L.ld, 1, 1, B.cols, {sg});
-            xoff += (long long)x.rows * x.cols;
+            xidx[{w, b}] = (int)xs.size();
+            xs.push_back({bl.m[iab], B.cols, iab, lb, b, -1, 0});
         }
     }
-    P->x_size = xoff;
-
     // MPO mix: Y[w2, o] = sum coef X[w, b]   (o = output block (iab, s1, s2))
-    std::map<std::pair<int, int>, std::vector<std::pair<const XB*, double>>> yterms;   // (o, w2)
+    std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> yterms;   // (o, w2)
     for (const auto& e : w12.nz) {
         for (int b = 0; b < nb; ++b) {
             const auto& B = pb[b];
             if (B.s1 != e.s1p || B.s2 != e.s2p) continue;
-            auto it = xb.find({e.w, b});
-            if (it == xb.end()) continue;
-            int o = P->psi.at(it->second.iab, e.s1, e.s2);
+            auto it = xidx.find({e.w, b});
+            if (it == xidx.end()) continue;
+            int o = P->psi.at(xs[it->second].iab, e.s1, e.s2);
             if (o < 0) continue;
             int rb = R.at(pb[o].k, e.w2);
             if (rb < 0) continue;
             PD_REQUIRE(R.blk[rb].k == B.k, DMRG_ERR_QN, "MPO flux rule violated in the two-site operator");
-            yterms[{o, e.w2}].push_back({&it->second, e.v});
+            yterms[{o, e.w2}].push_back({it->second, e.v});
+            xs[it->second].fan++;
         }
     }
-    // Y slab rows and R-stage segments per output block
-    std::map<int, std::vector<GSeg>> rsegs;
+    // Y slab rows
     long long yrow = 0;
+    std::map<std::pair<int, int>, long long> yrow_of;
     for (auto& kv : yterms) {
-        int o = kv.first.first, w2 = kv.first.second;
-        const XB* x0 = kv.second.front().first;
-        MixJob mj{};
-        mj.dst = yrow * P->ld_y;
-        mj.rows = x0->rows;
-        mj.cols = x0->cols;
-        mj.ldo = P->ld_y;
-        mj.zero_to = kpad(x0->cols, prec);
-        mj.t0 = (int)P->mix.terms.size();
-        mj.nt = (int)kv.second.size();
-        for (auto& t : kv.second) P->mix.terms.push_back({t.first->off, t.first->cols, 0, t.second});
-        P->mix.jobs.push_back(mj);
-        P->mix.max_elems = std::max(P->mix.max_elems, mj.rows * std::max(mj.cols, mj.zero_to));
-        P->mix.flops += 2.0 * mj.rows * mj.cols * mj.nt;
-        int rb = R.at(pb[o].k, w2);
-        rsegs[o].push_back({R.blk[rb].row * R.ld, yrow * P->ld_y, x0->cols, 0});
-        yrow += x0->rows;
+        yrow_of[kv.first] = yrow;
+        yrow += xs[kv.second.front().first].rows;
     }
     P->y_rows = yrow;
+    // direct targets
+    std::vector<long long> direct_row(xs.size(), -1);
+    std::vector<double> direct_coef(xs.size(), 0.0);
+    for (auto& kv : yterms)
+        if (kv.second.size() == 1 && xs[kv.second[0].first].fan == 1) {
+            direct_row[kv.second[0].first] = yrow_of[kv.first];
+            direct_coef[kv.second[0].first] = kv.second[0].second;
+        }
+    long long xoff = 0;
+    for (size_t xi = 0; xi < xs.size(); ++xi) {
+        XB& x = xs[xi];
+        const auto& B = pb[x.b];
+        GSeg sg{prow[x.b] * P->ld_psi, L.blk[x.lb].row * L.ld, B.rows, 0};
+        if (direct_row[xi] >= 0) {
+            P->ldirect.add(x.cols, x.rows, direct_row[xi] * P->ld_y, P->ld_psi, 1, L.ld, 1, 1, P->ld_y, {sg}, 0,
+                           direct_coef[xi]);
+        } else {
+            x.off = xoff;
+            P->lstage.add(x.cols, x.rows, xoff, P->ld_psi, 1, L.ld, 1, 1, x.cols, {sg});
+            xoff += (long long)x.rows * x.cols;
+        }
+    }
+    P->x_size = xoff;
+    // mixing jobs for the remaining Y blocks, R-stage segments for all of them
+    std::map<int, std::vector<GSeg>> rsegs;
+    for (auto& kv : yterms) {
+        int o = kv.first.first, w2 = kv.first.second;
+        const XB& x0 = xs[kv.second.front().first];
+        const long long yr = yrow_of[kv.first];
+        P->mix.flops += 2.0 * x0.rows * x0.cols * (double)kv.second.size();
+        const bool direct = kv.second.size() == 1 && direct_row[kv.second[0].first] >= 0;
+        if (!direct) {
+            MixJob mj{};
+            mj.dst = yr * P->ld_y;
+            mj.rows = x0.rows;
+            mj.cols = x0.cols;
+            mj.ldo = P->ld_y;
+            mj.zero_to = kpad(x0.cols, prec);
+            mj.t0 = (int)P->mix.terms.size();
+            mj.nt = (int)kv.second.size();
+            for (auto& t : kv.second) P->mix.terms.push_back({xs[t.first].off, xs[t.first].cols, 0, t.second});
+            P->mix.jobs.push_back(mj);
+            P->mix.max_elems = std::max(P->mix.max_elems, mj.rows * std::max(mj.cols, mj.zero_to));
+        }
+        int rb = R.at(pb[o].k, w2);
+        rsegs[o].push_back({R.blk[rb].row * R.ld, yr * P->ld_y, x0.cols, 0});
+    }
     for (auto& kv : rsegs) {
         const auto& O = pb[kv.first];
         P->rstage.add(O.cols, O.rows, O.off, R.ld, 1, P->ld_y, 1, 1, O.cols, kv.second);
@@ -529,7 +559,7 @@ std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std
         P->diag_max = std::max(P->diag_max, B.rows * B.cols);
     }
 
-    P->flops = P->lstage.flops + P->rstage.flops + P->mix.flops;
+    P->flops = P->lstage.flops + P->ldirect.flops + P->rstage.flops + P->mix.flops;
     // upload static lists
     P->pack.up(st);
     P->mix.up(st);
@@ -545,6 +575,8 @@ std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std
     const Num t = mv_num(prec);
     P->psiT.ensure(std::max<long long>(1, P->psiT_rows) * P->ld_psi * num_size(t), st);
     P->Y.ensure(std::max<long long>(1, P->y_rows) * P->ld_y * num_size(t), st);
+    // directly written Y blocks rely on zero padding columns: clear the slab once
+    PD_CK(cudaMemsetAsync(P->Y.p, 0, std::max<long long>(1, P->y_rows) * P->ld_y * num_size(t), st));
     P->X.ensure(std::max<long long>(1, P->x_size) * (prec == DMRG_FP64 ? 8 : 4), st);
     PD_REQUIRE(P->psi.size < (1LL << 31), DMRG_ERR_CAPACITY, "two-site vector too long for one copy job");
     return P;
@@ -567,6 +599,7 @@ void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x
     PD_CK(cudaMemsetAsync(y, 0, sizeof(double) * std::max<long long>(P.psi.size, 1), st));
     if (prec == DMRG_FP64) {
         run_gemm64(P.lstage, P.psiT.as<double>(), L.buf.as<double>(), P.X.as<double>(), st);
+        run_gemm64(P.ldirect, P.psiT.as<double>(), L.buf.as<double>(), P.Y.as<double>(), st);
         run_mix<double>(P.mix, P.X.as<double>(), P.Y.p, Num::F64, st);
         run_gemm64(P.rstage, R.buf.as<double>(), P.Y.as<double>(), y, st);
     } else if (prec == PREC_F32) {
@@ -575,6 +608,7 @@ void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x
         y32.ensure(std::max<long long>(1, P.psi.size) * 4, st);
         PD_CK(cudaMemsetAsync(y32.p, 0, std::max<long long>(1, P.psi.size) * 4, st));
         run_gemm32(P.lstage, P.psiT.as<float>(), L.buf.as<float>(), P.X.as<float>(), st);
+        run_gemm32(P.ldirect, P.psiT.as<float>(), L.buf.as<float>(), P.Y.as<float>(), st);
         run_mix<float>(P.mix, P.X.as<float>(), P.Y.p, Num::F32, st);
         run_gemm32(P.rstage, R.buf.as<float>(), P.Y.as<float>(), y32.as<float>(), st);
         if (!P.unpack.d.p) {
@@ -587,9 +621,12 @@ void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x
         run_copy<float>(P.unpack, y32.as<float>(), y, Num::F64, st);
     } else {
         run_gemm_tc(P.lstage, t, P.psiT.p, P.psiT_rows, P.ld_psi, env_operand(L, prec), L.lay.rows, L.lay.ld,
-                    P.X.p, false, err, st);
+                    P.X.p, Num::F32, err, st);
+        run_gemm_tc(P.ldirect, t, P.psiT.p, P.psiT_rows, P.ld_psi, env_operand(L, prec), L.lay.rows, L.lay.ld,
+                    P.Y.p, t, err, st);
         run_mix<float>(P.mix, P.X.as<float>(), P.Y.p, t, st);
-        run_gemm_tc(P.rstage, t, env_operand(R, prec), R.lay.rows, R.lay.ld, P.Y.p, P.y_rows, P.ld_y, y, true, err, st);
+        run_gemm_tc(P.rstage, t, env_operand(R, prec), R.lay.rows, R.lay.ld, P.Y.p, P.y_rows, P.ld_y, y, Num::F64,
+                    err, st);
     }
 }
 

@@ -177,7 +177,7 @@ struct GemmBatch {
 void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st);
 void run_gemm32(GemmBatch& g, const float* A, const float* B, float* C, cudaStream_t st);
 void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B,
-                 long long b_rows, int ldb, void* C, bool c_is_f64, unsigned* err, cudaStream_t st);
+                 long long b_rows, int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st);
 bool tc_available();
 
 // ------------------------------------------------------------------------------------------
@@ -260,7 +260,7 @@ struct HeffPlan {
     long long psiT_rows = 0, y_rows = 0, x_size = 0;
     CopyList pack;            // canonical x -> psiT slab
     CopyList unpack;          // FP32 result -> FP64 (accurate refinement plan)
-    GemmBatch lstage, rstage;
+    GemmBatch lstage, ldirect, rstage;   // L stage into X / straight into Y, R stage
     MixList mix;              // X -> Y slab
     std::vector<DiagJob> djobs;
     std::vector<DiagTerm> dterms;

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "plans.h"
 
@@ -294,8 +295,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                             OutT* dst = crow + (long long)(tl.n0 + n) * p.scn;
                             float v = __uint_as_float(r[j]);
                             if (scale) v *= alpha;
-                            if (accum) *dst = *dst + (OutT)v;
-                            else *dst = (OutT)v;
+                            if constexpr (std::is_same<OutT, double>::value) {
+                                *dst = accum ? *dst + (double)v : (double)v;
+                            } else {
+                                if (accum) v += (float)*dst;
+                                *dst = (OutT)v;
+                            }
                         }
                     }
                 }
@@ -413,7 +418,7 @@ bool tc_available() {
 }
 
 void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B, long long b_rows,
-                 int ldb, void* C, bool c_is_f64, unsigned* err, cudaStream_t st) {
+                 int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st) {
     if (g.empty()) return;
     PD_REQUIRE(t == Num::BF16 || t == Num::F32, DMRG_ERR_ARG, "tensor-core operands must be bf16 or fp32");
     PD_REQUIRE(err != nullptr, DMRG_ERR_ARG, "tensor-core GEMM needs a device error word");
@@ -425,10 +430,11 @@ void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, 
     const CUtensorMap ma = make_map(t, A, a_rows, lda, BM);
     const CUtensorMap mb = make_map(t, B, b_rows, ldb, bn);
     const bool bf = t == Num::BF16;
-#define PD_TC(KIND, BN, ST)                                                                     \
-    do {                                                                                        \
-        if (c_is_f64) launch_tc<KIND, BN, ST, double>(g, ma, mb, lda, ldb, C, err, st);         \
-        else launch_tc<KIND, BN, ST, float>(g, ma, mb, lda, ldb, C, err, st);                   \
+#define PD_TC(KIND, BN, ST)                                                                       \
+    do {                                                                                          \
+        if (cnum == Num::F64) launch_tc<KIND, BN, ST, double>(g, ma, mb, lda, ldb, C, err, st);   \
+        else if (cnum == Num::F32) launch_tc<KIND, BN, ST, float>(g, ma, mb, lda, ldb, C, err, st); \
+        else launch_tc<KIND, BN, ST, __nv_bfloat16>(g, ma, mb, lda, ldb, C, err, st);             \
     } while (0)
     if (bn == 256) {
         if (bf) PD_TC(0, 256, 4); else PD_TC(1, 256, 4);
