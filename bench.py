@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["steps", "op"], default="steps",
-                    help="op: repeated H_eff matvecs at one bond (random environments) -- small device "
-                         "footprint, used for profiler captures")
+    ap.add_argument("--mode", choices=["steps", "sweeps", "op"], default="steps",
+                    help="sweeps: a step is one real-space parallel sweep (Fig. 4) over the whole lattice; "
+                         "steps: a step is one bulk two-site update (serial); op: repeated H_eff matvecs at "
+                         "one bond (random environments, small device footprint, for profiler captures)")
+    ap.add_argument("--regions", type=int, default=4)
     return ap.parse_args()
 
 
@@ -101,8 +103,12 @@ def workload(args):
     mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
     qn = list(mpo.site.qn)
     L = mpo.L
-    center = L // 2 - (args.warmup + args.steps) // 2
-    mps = wl.isometric_mps(L, qn, 0, args.m, args.seed, center, sigma=args.sigma)
+    if args.mode == "sweeps":
+        center = 0
+        mps = wl.isometric_mps(L, qn, 0, args.m, args.seed, 0, sigma=args.sigma)
+    else:
+        center = L // 2 - (args.warmup + args.steps) // 2
+        mps = wl.isometric_mps(L, qn, 0, args.m, args.seed, center, sigma=args.sigma)
     return mpo, qn, mps, center
 
 
@@ -266,7 +272,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        sample = oracle_sample(mpo, qn, mps, center)
+        sample_bond = L // 2 - 1
+        sample = oracle_sample(mpo, qn, mps, sample_bond)
         for _ in range(args.warmup):
             time_oracle(sample, 0.0)
         vals, t_all = [], 0.0
@@ -282,9 +289,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}",
-                       "D": max(mpo.D), "m": args.m, "bond": center, "precision": "fp64-oracle"},
+                       "D": max(mpo.D), "m": args.m, "bond": sample_bond, "precision": "fp64-oracle"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"one full H_eff matvec of the CPU oracle per step at bond {center} "
+                             "sample": f"one full H_eff matvec of the CPU oracle per step at bond {sample_bond} "
                                        f"of the {args.lx}x{args.ly} m={args.m} state (random environments "
                                        "with that bond's block structure)"},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -306,11 +313,16 @@ def main():
     data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
     t_setup = time.perf_counter()
     eng.set_mps(mps.bonds, data, center=center)
-    t_setup = time.perf_counter() - t_setup
     # a fixed number of Davidson steps: tensor-core iterations, then an FP32-accurate refinement
     dav = dict(dav_tol=0.0, dav_max_iter=args.dav_iters, refine_iters=args.refine_iters)
+    if args.mode == "sweeps":
+        eng.setup_regions(args.regions, 0, args.m, **dav)
+        run_step = lambda: eng.sweep(args.m, **dav)
+    else:
+        run_step = lambda: eng.advance(1, args.m, **dav)
+    t_setup = time.perf_counter() - t_setup
     for _ in range(args.warmup):
-        eng.advance(1, args.m, **dav)
+        run_step()
     torch.cuda.synchronize()
     pd.profile_reset()
     pd.profile_enable(True)
@@ -325,7 +337,7 @@ def main():
     w0 = time.perf_counter()
     ev0.record()
     for _ in range(args.steps):
-        stats.append(eng.advance(1, args.m, **dav))    # host params in, host stats out per step
+        stats.append(run_step())    # host parameters in, host statistics out, every step
     ev1.record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
@@ -363,18 +375,21 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}", "D": max(mpo.D),
-                   "m": args.m, "sectors_at_bond": len(mps.bonds[center + 1]), "bond_start": center,
+                   "m": args.m, "sectors_at_centre": len(mps.bonds[L // 2]), "step": args.mode,
                    "dav_iters": args.dav_iters, "refine_iters": args.refine_iters, "kmax": args.kmax,
-                   "precision": args.precision,
-                   "regions": 1, "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
+                   "precision": args.precision, "regions": args.regions if args.mode == "sweeps" else 1,
+                   "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
                    "setup_s": t_setup},
-        "sweep_s": ms_step * 2 * (L - 1) / 1e3,
-        "sweep_s_note": "bulk step time at m=2000 x 2(L-1) steps",
+        "sweep_s": ms_step / 1e3 if args.mode == "sweeps" else ms_step * 2 * (L - 1) / 1e3,
+        "sweep_s_note": ("one real-space parallel sweep, measured" if args.mode == "sweeps"
+                         else "bulk step time at m=2000 x 2(L-1) steps"),
+        "merge_fidelity_max": max(s["max_fidelity"] for s in stats) if args.mode == "sweeps" else None,
         "matvecs": sum(s["n_matvec"] for s in stats),
         "refine_matvecs": sum(s["n_refine_matvec"] for s in stats),
         "refine_matvec_ms": 1e3 * sum(s["refine_seconds"] for s in stats) / max(1, sum(s["n_refine_matvec"] for s in stats)),
         "matvec_ms": 1e3 * mv_s / max(1, sum(s["n_matvec"] for s in stats)),
         "energy_last_step": stats[-1]["energy"],
+        "max_trunc_err": max(s["max_trunc_err"] for s in stats),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": ctypes.sizeof(pd.SweepParams),
@@ -386,10 +401,11 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = oracle_sample(mpo, qn, mps, center)
+        sample_bond = L // 2 - 1
+        sample = oracle_sample(mpo, qn, mps, sample_bond)
         v, reps, t = time_oracle(sample, args.cpu_sample_s)
         out["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": blas_threads(), "kind": "oracle",
-                               "sample": f"{reps} H_eff matvecs of the CPU oracle ({t:.1f} s) at bond {center} "
+                               "sample": f"{reps} H_eff matvecs of the CPU oracle ({t:.1f} s) at bond {sample_bond} "
                                          "with random environments of that bond's block structure"}
     if rank == 0:
         print(json.dumps(out))

@@ -181,9 +181,11 @@ void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, T* V, cudaStream
 // All Jacobi sweeps (until a sweep without rotation, at most max_sweeps) in one cooperative launch.
 // Pairs whose smaller column norm is below eta * |W_sector|_F are not rotated (eta = 0: all are).
 // floor2: nsec doubles of scratch.
+// bar: 3 unsigned words of scratch for the bounded grid barrier; err: device error word.
 template <class T>
 void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs, int maxnpad, int max_sweeps, T* W,
-                   T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, cudaStream_t st);
+                   T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, unsigned* bar, unsigned* err,
+                   cudaStream_t st);
 template <class T>
 void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st);
 

@@ -7,15 +7,12 @@
 //  * Davidson       dot products, Ritz vectors, residuals, Gram-Schmidt, small Jacobi eigensolver
 //  * SVD            batched one-sided (Hestenes) Jacobi SVD per charge sector, Eq. (svd)
 //  * truncation     global keep-largest-m selection over all sectors (single CTA)
-#include <cooperative_groups.h>
-
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
 
 #include "internal.h"
 
-namespace cg = cooperative_groups;
 
 namespace pd {
 
@@ -426,29 +423,72 @@ __device__ __forceinline__ bool jacobi_pair(const SvdSec& s, int pi, int round, 
     return true;
 }
 
-// All sweeps of all sectors in one cooperative launch; grid-wide sync between rounds.
-// rot[sweep] counts the rotations of that sweep (zeroed by the host); *sweeps = sweeps run.
+// Grid-wide barrier with a time bound (the launch is cooperative, so all blocks are resident).
+// bar[0] = arrival count, bar[1] = generation, bar[2] = abort flag.  On expiry the block sets
+// ERRBIT_TIMEOUT and the abort flag, and every later barrier returns false at once.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vbar = bar;
+        int ok = vbar[2] == 0u;
+        if (ok) {
+            const unsigned gen = vbar[1];
+            __threadfence();
+            if (atomicAdd(&bar[0], 1u) == nblocks - 1u) {
+                atomicExch(&bar[0], 0u);
+                __threadfence();
+                atomicAdd(&bar[1], 1u);
+            } else {
+                uint64_t t0;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+                while (vbar[1] == gen) {
+                    if (vbar[2]) { ok = 0; break; }
+                    uint64_t t;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (t - t0 > 2000000000ull) {
+                        atomicOr(err, ERRBIT_TIMEOUT);
+                        atomicExch(&bar[2], 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// All sweeps of all sectors in one cooperative launch; bounded grid barrier between rounds.
+// rot[sweep] counts the warps that rotated in that sweep (zeroed by the host); *sweeps = sweeps
+// run; bar: 3 zeroed words for the barrier.
 template <class T>
 __global__ void k_jacobi_coop(const SvdSec* __restrict__ secs, const int* __restrict__ pair_sec, int npairs,
                               int maxnpad, int max_sweeps, T* __restrict__ W, T* __restrict__ V, T tol,
-                              const double* __restrict__ floor2, int* __restrict__ rot, int* __restrict__ sweeps) {
-    cg::grid_group grid = cg::this_grid();
+                              const double* __restrict__ floor2, int* __restrict__ rot, int* __restrict__ sweeps,
+                              unsigned* __restrict__ bar, unsigned* __restrict__ err) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     int sweep = 0;
-    for (; sweep < max_sweeps; ++sweep) {
+    bool alive = true;
+    for (; sweep < max_sweeps && alive; ++sweep) {
         int mine = 0;
-        for (int round = 0; round < maxnpad - 1; ++round) {
+        for (int round = 0; round < maxnpad - 1 && alive; ++round) {
             for (int w = gw; w < npairs; w += nw) {
                 const int si = pair_sec[w];
                 const SvdSec s = secs[si];
                 if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, (T)floor2[si], lane)) mine = 1;
             }
-            grid.sync();
+            alive = grid_barrier(bar, gridDim.x, err);
         }
+        if (!alive) break;
         if (lane == 0 && mine) atomicAdd(&rot[sweep], 1);
-        grid.sync();
+        alive = grid_barrier(bar, gridDim.x, err);
+        if (!alive) break;
         if (*((volatile int*)&rot[sweep]) == 0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = sweep + 1;
@@ -702,7 +742,8 @@ template void launch_svd_init_v<float>(const SvdSec*, int, int, float*, cudaStre
 
 template <class T>
 void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs, int maxnpad, int max_sweeps, T* W,
-                   T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, cudaStream_t st) {
+                   T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, unsigned* bar, unsigned* err,
+                   cudaStream_t st) {
     if (npairs <= 0 || maxnpad < 2) return;
     k_svd_floor<T><<<nsec, 256, 0, st>>>(secs, W, eta, floor2);
     PD_LAUNCHED();
@@ -716,15 +757,17 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
     int need = (npairs * 32 + threads - 1) / threads;
     int blocks = std::max(1, std::min(need, ps * sms));
     const double* fl = floor2;
+    PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
     void* args[] = {(void*)&secs, (void*)&pair_sec, (void*)&npairs, (void*)&maxnpad, (void*)&max_sweeps,
-                    (void*)&W, (void*)&V, (void*)&tol, (void*)&fl, (void*)&rot, (void*)&sweeps};
+                    (void*)&W, (void*)&V, (void*)&tol, (void*)&fl, (void*)&rot, (void*)&sweeps, (void*)&bar,
+                    (void*)&err};
     PD_CK(cudaLaunchCooperativeKernel((void*)k_jacobi_coop<T>, blocks, threads, args, 0, st));
     PD_LAUNCHED();
 }
 template void launch_jacobi<double>(const SvdSec*, int, const int*, int, int, int, double*, double*, double, double,
-                                    double*, int*, int*, cudaStream_t);
+                                    double*, int*, int*, unsigned*, unsigned*, cudaStream_t);
 template void launch_jacobi<float>(const SvdSec*, int, const int*, int, int, int, float*, float*, float, double,
-                                   double*, int*, int*, cudaStream_t);
+                                   double*, int*, int*, unsigned*, unsigned*, cudaStream_t);
 
 template <class T>
 void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st) {

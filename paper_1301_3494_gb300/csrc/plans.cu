@@ -1091,9 +1091,13 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         }
         gather.add(j);
     }
-    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dfloor;
+    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dfloor, dbar;
     const int max_sweeps = 60;
     dfloor.ensure(std::max(1, nsec) * 8, st);
+    dbar.ensure(4 * sizeof(unsigned), st);     // barrier words + the error word
+    PD_CK(cudaMemsetAsync(dbar.p, 0, 4 * sizeof(unsigned), st));
+    unsigned* bar = dbar.as<unsigned>();
+    unsigned* jerr = bar + 3;
     dW.ensure(std::max<long long>(1, woff) * es, st);
     dV.ensure(std::max<long long>(1, voff) * es, st);
     dsig.ensure(std::max<long long>(1, soff) * 8, st);
@@ -1121,7 +1125,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)maxp));
         launch_jacobi<float>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, 40, dW.as<float>(),
                              dV.as<float>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(), drot.as<int>() + max_sweeps,
-                             st);
+                             bar, jerr, st);
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
         run_copy<double>(gather, psi, dW.p, Num::F64, st);
@@ -1129,7 +1133,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
         launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps,
                               dW.as<double>(), dV.as<double>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(),
-                              drot.as<int>() + max_sweeps, st);
+                              drot.as<int>() + max_sweeps, bar, jerr, st);
         launch_svd_finish<double>(dsecs.as<SvdSec>(), nsec, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
     }
     if (sv0) {
@@ -1146,13 +1150,19 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     DBuf tsd, tsi;
     tsd.ensure((size_t)(total + nsec + 1) * 8, st);
     tsi.ensure((size_t)(3 * total + 1) * 4, st);
-    launch_truncate(dsecs.as<SvdSec>(), nsec, dsig.as<double>(), dord.as<int>(), total, m_max, rel_cutoff, 1e-10,
+    // an FP32 SVD reports exact zeros at ~1e-7 of the largest singular value: keep its cutoff
+    // above that noise floor (the discarded weight stays below 1e-10)
+    const double cutoff = fp32 ? std::max(rel_cutoff, 1e-5) : rel_cutoff;
+    launch_truncate(dsecs.as<SvdSec>(), nsec, dsig.as<double>(), dord.as<int>(), total, m_max, cutoff, 1e-10,
                     dkept.as<int>(), dwts.as<double>(), tsd.as<double>(), tsi.as<int>(), st);
     std::vector<int> kept(nsec);
     double wts[2];
+    unsigned jerr_h = 0;
+    PD_CK(cudaMemcpyAsync(&jerr_h, jerr, 4, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(kept.data(), dkept.p, 4 * nsec, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(wts, dwts.p, 16, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
+    PD_REQUIRE(!(jerr_h & ERRBIT_TIMEOUT), DMRG_ERR_TIMEOUT, "Jacobi SVD grid barrier timed out");
     SplitResult res;
     std::vector<int> kept_of_sec(nsec, 0);
     for (int s = 0; s < nsec; ++s)
