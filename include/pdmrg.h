@@ -277,7 +277,10 @@ dmrg_status dmrg_env_right(const dmrg_bond_desc* bd, int prec, const double* Rin
  * the left bond x new middle bond), lambda, B (packed site tensor middle x right).  The kept
  * set: lambda <= 1e-12 lambda_max dropped; order (lambda desc, q asc, index asc); first m_max
  * kept; a degenerate group at the cut (relative gap <= 1e-10) dropped whole.  lambda is
- * normalised to sum lambda^2 = 1.  accurate != 0 applies the Appendix recursion (eps 1e-4).
+ * normalised to sum lambda^2 = 1.  `accurate` selects the mode: 0 FP64 one-sided Jacobi; 1 the
+ * same with the Appendix recursion (eps 1e-4); 2 the mixed-precision engine's split: FP32 block
+ * Jacobi, cutoff raised to 1e-5 lambda_max (above the FP32 rounding level), A re-orthonormalised
+ * in FP64 (Newton-Schulz), B = V^T as computed in FP32.  Other values: DMRG_ERR_ARG.
  * Outputs: middle-bond sectors (nm_out, qm_out[cap], mm_out[cap]), A_dev/B_dev/lam_dev sized
  * by the caller for the worst case (no truncation), trunc_out (nullable) the discarded weight.
  * Synchronises the stream (the kept sector sizes are returned to the host). */

@@ -206,12 +206,13 @@ def env_right(bond: Bond, prec, Rin_dev, B_dev, Rout_dev, stream=0):
 
 
 def svd_split(bond: Bond, psi_dev, m_max, accurate, A_dev, lam_dev, B_dev, cap=4096, stream=0):
-    """Returns (middle-bond sectors dict, discarded weight)."""
+    """Returns (middle-bond sectors dict, discarded weight).  accurate: False/0 FP64 Jacobi,
+    True/1 with the accurate recursion, 2 the FP32 block-Jacobi split of the mixed-precision engine."""
     nm = C.c_int(0)
     qm = np.zeros(cap, np.int32)
     mm = np.zeros(cap, np.int32)
     tr = C.c_double(0.0)
-    _check(lib().dmrg_svd_split(C.byref(bond.desc), psi_dev, int(m_max), int(bool(accurate)), A_dev, lam_dev, B_dev,
+    _check(lib().dmrg_svd_split(C.byref(bond.desc), psi_dev, int(m_max), int(accurate), A_dev, lam_dev, B_dev,
                                 cap, C.byref(nm), _ptr(qm, _ip), _ptr(mm, _ip), C.byref(tr), stream))
     return {int(q): int(m) for q, m in zip(qm[: nm.value], mm[: nm.value])}, tr.value
 

@@ -176,7 +176,11 @@ dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int 
         cudaStream_t st = (cudaStream_t)stream;
         std::vector<int> qn(bd->qn_local, bd->qn_local + bd->d);
         Sec bl = make_sec(bd->nl, bd->ql, bd->ml), br = make_sec(bd->nr, bd->qr, bd->mr);
-        SplitResult r = svd_split(bl, br, qn, qn, psi_dev, m_max, 1e-12, accurate != 0, 0, 0, A_dev, B_dev, lam_dev, st);
+        PD_REQUIRE(accurate >= 0 && accurate <= 2, DMRG_ERR_ARG, "mode must be 0, 1 or 2");
+        const bool fp32 = accurate == 2;
+        SplitResult r = svd_split(bl, br, qn, qn, psi_dev, m_max, 1e-12, accurate == 1, 0, 0, A_dev, B_dev, lam_dev, st,
+                                  fp32);
+        if (fp32) orthonormalize_factor(bl, r.mid, qn, A_dev, true, st);
         PD_REQUIRE(r.mid.n() <= cap, DMRG_ERR_CAPACITY, "output sector capacity too small");
         *nm_out = r.mid.n();
         for (int i = 0; i < r.mid.n(); ++i) {

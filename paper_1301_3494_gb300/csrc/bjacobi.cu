@@ -1,0 +1,429 @@
+// Block one-sided Jacobi SVD in FP32 for the charge sectors of the two-site wavefunction
+// (the decomposition of Eq. (svd), Sec. II).
+//
+// The columns of every sector matrix W (p x n, column-major, n <= p) are cut into blocks of 16.
+// A sweep pairs every block with every other block once (round-robin ordering of the blocks);
+// a round processes all pairs of all sectors at once, one pair per CTA, and ends in a bounded
+// grid barrier.  For a pair (I, J), I < J, the CTA stages the p x 32 columns in shared memory,
+// forms their 32 x 32 Gram matrix, diagonalises it with a few sweeps of two-sided cyclic
+// Jacobi, orders the eigenvectors by decreasing eigenvalue (block I receives the larger ones),
+// and rotates the staged columns and the matching columns of V by that orthogonal matrix.  The
+// sector has converged when a sweep finds no pair to rotate; the test of a pair is computed from
+// the current columns, so the inexact inner solve is corrected by the next visit.
+//
+// Compared with rotating single column pairs, the number of grid-wide synchronisations per
+// sweep drops from n - 1 to n / 16 - 1, and the work of a round becomes dense (Gram matrix and
+// a 32-column rotation per CTA).
+//
+// A pair of columns (u, v) is rotated when |g_uv| > tol * |w_u| |w_v| + noise * (|w_u| + |w_v|),
+// with noise = c * eps_f32 * sigma_max: the second term is the absolute rounding level of FP32
+// columns of a matrix whose largest singular value is sigma_max.  Pairs below it are left as
+// they are; their effect on the kept weight is below eps_f32 * sigma_max^2.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "grid_sync.cuh"
+#include "internal.h"
+
+namespace pd {
+
+namespace {
+
+constexpr int BJ_B = 16;                     // columns per block
+constexpr int BJ_K = 2 * BJ_B;               // columns of a block pair (= warp width)
+constexpr int BJ_NP = BJ_K / 2;              // column pairs per inner round
+constexpr int BJ_LD = BJ_K + 1;              // row stride of staged rows (conflict-free)
+constexpr int BJ_QLD = BJ_K + 4;             // row stride of rotations (16-byte aligned rows)
+constexpr int BJ_THREADS = 256;
+constexpr int BJ_WARPS = BJ_THREADS / 32;
+constexpr int BJ_SMEM_MAX = 227 * 1024;
+
+struct alignas(16) BjShared {
+    float G[BJ_K * BJ_LD];             // Gram matrix (rotated in place)
+    float Q[2][BJ_K * BJ_QLD];         // accumulated rotation; its column-permuted copy
+    float Gp[BJ_WARPS][BJ_K * BJ_K];   // per-warp partial Gram matrices
+    float c[BJ_NP], s[BJ_NP];          // rotation of each pair of the current inner round
+    float diag[BJ_K];
+    int gcol[BJ_K];                    // sector column of staged column u (-1: padding)
+    int perm[BJ_K];                    // perm[r] = eigenvector placed at position r
+    unsigned char lo[BJ_K - 1][BJ_NP], hi[BJ_K - 1][BJ_NP];   // inner round-robin pairs
+    float noise;
+    int flag[2];                       // any rotation in the inner round (by round parity)
+};
+static_assert(sizeof(BjShared) % 16 == 0, "staging area must stay 16-byte aligned");
+
+__device__ __forceinline__ int rr_pos(int pos, int round, int npad) {
+    return pos == 0 ? 0 : ((pos - 1 + round) % (npad - 1)) + 1;
+}
+
+__device__ __forceinline__ bool bj_need(float guv, float guu, float gvv, float tol, float noise) {
+    if (!(guu > 0.f) || !(gvv > 0.f)) return false;
+    const float su = guu * rsqrtf(guu), sv = gvv * rsqrtf(gvv);   // approximate roots: a threshold
+    return fabsf(guv) > tol * su * sv + noise * (su + sv);
+}
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// X[r][u] = src[gcol[u] * rows + r] (zero for padding columns), as asynchronous copies
+// (the caller commits and waits).
+__device__ __forceinline__ void bj_stage_async(float* __restrict__ X, const float* __restrict__ src, int rows,
+                                               const int* __restrict__ gcol) {
+    for (int u = 0; u < BJ_K; ++u) {
+        const int c = gcol[u];
+        if (c >= 0) {
+            const float* col = src + (long long)c * rows;
+            for (int r = threadIdx.x; r < rows; r += BJ_THREADS) cp_async4(X + r * BJ_LD + u, col + r);
+        } else {
+            for (int r = threadIdx.x; r < rows; r += BJ_THREADS) X[r * BJ_LD + u] = 0.f;
+        }
+    }
+}
+
+// dst[gcol[u] * rows + r] = X[r][u] for u < k: a thread reads a whole staged row, then stores
+// it to the k columns (coalesced across the warp).
+__device__ __forceinline__ void bj_unstage(const float* __restrict__ X, float* __restrict__ dst, int rows,
+                                           const int* __restrict__ gcol, int k) {
+    int cols[BJ_K];
+#pragma unroll
+    for (int u = 0; u < BJ_K; ++u) cols[u] = gcol[u];
+    for (int r = threadIdx.x; r < rows; r += BJ_THREADS) {
+        float v[BJ_K];
+#pragma unroll
+        for (int u = 0; u < BJ_K; ++u) v[u] = X[r * BJ_LD + u];
+#pragma unroll
+        for (int u = 0; u < BJ_K; ++u)
+            if (u < k) dst[(long long)cols[u] * rows + r] = v[u];
+    }
+}
+
+// S.G = X^T X over `rows` staged rows.  Lane: an 8 x 8 tile of one of two interleaved row
+// halves of the warp's rows; halves summed by shuffle, warps summed in warp order.
+__device__ __forceinline__ void bj_gram(BjShared& S, const float* __restrict__ X, int rows) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u0 = 8 * (lane & 3), v0 = 8 * ((lane >> 2) & 3), half = lane >> 4;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int r = 2 * w + half; r < rows; r += 2 * BJ_WARPS) {
+        const float* xr = X + r * BJ_LD;
+        float a[8], b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = xr[u0 + i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = xr[v0 + j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], 16);
+    if (half == 0) {
+        float* gp = S.Gp[w];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) gp[(u0 + i) * BJ_K + v0 + j] = acc[i][j];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BJ_K * BJ_K; e += BJ_THREADS) {
+        float g = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < BJ_WARPS; ++ww) g += S.Gp[ww][e];
+        S.G[(e >> 5) * BJ_LD + (e & 31)] = g;
+    }
+}
+
+// X <- X Qp in place over `rows` staged rows.  Lane: 8 output columns of 4 rows; a warp owns
+// 32 consecutive rows per pass.
+__device__ __forceinline__ void bj_rotate(float* __restrict__ X, const float* __restrict__ Qp, int rows) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c0 = 8 * (lane & 3), rg = lane >> 2;
+    for (int rb = w * 32; rb < rows; rb += BJ_WARPS * 32) {
+        int r[4];
+        bool ok[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            r[i] = rb + rg + 8 * i;
+            ok[i] = r[i] < rows;
+        }
+        float acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+        for (int u = 0; u < BJ_K; ++u) {
+            float x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = ok[i] ? X[r[i] * BJ_LD + u] : 0.f;
+            const float4 qa = *reinterpret_cast<const float4*>(Qp + u * BJ_QLD + c0);
+            const float4 qb = *reinterpret_cast<const float4*>(Qp + u * BJ_QLD + c0 + 4);
+            const float q[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(x[i], q[j], acc[i][j]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (ok[i])
+#pragma unroll
+                for (int j = 0; j < 8; ++j) X[r[i] * BJ_LD + c0 + j] = acc[i][j];
+        __syncwarp();
+    }
+}
+
+// Rotation (c, s) annihilating g_pq of the pair (p, q): new_p = c p - s q, new_q = s p + c q.
+// The angle may be slightly inexact (fast reciprocals; the next visit corrects it), but c and s
+// are normalised to c^2 + s^2 = 1 within an ulp (one Newton step on the reciprocal root), since
+// the accumulated rotations must stay orthogonal.
+__device__ __forceinline__ void bj_rot(float gpp, float gqq, float gpq, float& c, float& s) {
+    const float zeta = __fdividef(gqq - gpp, 2.f * gpq);
+    const float az = fabsf(zeta);
+    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); for huge |zeta|, t ~ 1 / (2 zeta)
+    float t = az < 1e18f ? __fdividef(1.f, az + sqrtf(fmaf(az, az, 1.f))) : __fdividef(0.5f, az);
+    t = zeta >= 0.f ? t : -t;
+    const float x = fmaf(t, t, 1.f);
+    float y = rsqrtf(x);
+    y = y * fmaf(-0.5f * x * y, y, 1.5f);
+    c = y;
+    s = y * t;
+}
+
+// Two-sided cyclic Jacobi on the Gram matrix S.G (in place) with the rotation accumulated in
+// S.Q[0]; at most `sweeps` sweeps, fewer when a sweep rotates nothing.  Each inner round: the
+// first half-warp decides the 16 rotations; then every thread rotates one 2 x 2 block of G (rows
+// of pair t / 16, columns of pair t % 16; the blocks partition G, so in place) and two column
+// pairs of one row of Q.
+__device__ __forceinline__ void bj_inner(BjShared& S, int sweeps, float tol, float noise) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < BJ_K * BJ_K; e += BJ_THREADS) S.Q[0][(e >> 5) * BJ_QLD + (e & 31)] = (e >> 5) == (e & 31);
+    const int bi = tid >> 4, bj = tid & 15;          // G block
+    const int qu = tid >> 3, qj = 2 * (tid & 7);      // Q row, first column pair
+    float* Qr = S.Q[0] + qu * BJ_QLD;
+    for (int isw = 0; isw < sweeps; ++isw) {
+        int any_sweep = 0;
+        for (int rnd = 0; rnd < BJ_K - 1; ++rnd) {
+            if (tid < 32) {
+                int rot = 0;
+                if (tid < BJ_NP) {
+                    const int p = S.lo[rnd][tid], q = S.hi[rnd][tid];
+                    const float gpp = S.G[p * BJ_LD + p], gqq = S.G[q * BJ_LD + q], gpq = S.G[p * BJ_LD + q];
+                    float c = 1.f, sn = 0.f;
+                    if (bj_need(gpq, gpp, gqq, tol, noise)) {
+                        bj_rot(gpp, gqq, gpq, c, sn);
+                        rot = 1;
+                    }
+                    S.c[tid] = c;
+                    S.s[tid] = sn;
+                }
+                const unsigned b = __ballot_sync(0xffffffffu, rot);
+                if (tid == 0) S.flag[rnd & 1] = b != 0u;
+            }
+            __syncthreads();
+            if (!S.flag[rnd & 1]) continue;   // nothing rotated: G and Q unchanged this round
+            any_sweep = 1;
+            {
+                const int p0 = S.lo[rnd][bi], q0 = S.hi[rnd][bi], p1 = S.lo[rnd][bj], q1 = S.hi[rnd][bj];
+                const float ci = S.c[bi], si = S.s[bi], cj = S.c[bj], sj = S.s[bj];
+                float* G = S.G;
+                const float a = G[p0 * BJ_LD + p1], b = G[p0 * BJ_LD + q1];
+                const float c = G[q0 * BJ_LD + p1], d = G[q0 * BJ_LD + q1];
+                // columns (p1, q1) by (cj, sj), then rows (p0, q0) by (ci, si)
+                const float a1 = cj * a - sj * b, b1 = sj * a + cj * b;
+                const float c1 = cj * c - sj * d, d1 = sj * c + cj * d;
+                G[p0 * BJ_LD + p1] = ci * a1 - si * c1;
+                G[q0 * BJ_LD + p1] = si * a1 + ci * c1;
+                G[p0 * BJ_LD + q1] = ci * b1 - si * d1;
+                G[q0 * BJ_LD + q1] = si * b1 + ci * d1;
+            }
+            {
+                const int pa = S.lo[rnd][qj], qa = S.hi[rnd][qj];
+                const int pb = S.lo[rnd][qj + 1], qb = S.hi[rnd][qj + 1];
+                const float ca = S.c[qj], sa = S.s[qj], cb = S.c[qj + 1], sb = S.s[qj + 1];
+                const float xa = Qr[pa], ya = Qr[qa], xb = Qr[pb], yb = Qr[qb];
+                Qr[pa] = ca * xa - sa * ya;
+                Qr[qa] = sa * xa + ca * ya;
+                Qr[pb] = cb * xb - sb * yb;
+                Qr[qb] = sb * xb + cb * yb;
+            }
+            __syncthreads();
+        }
+        if (!any_sweep) break;
+    }
+}
+
+// One block pair.  Returns true (in every thread) if it rotated.  XW: p staged rows; XV: n
+// staged rows (may alias XW, then V is staged after W has been written back).
+__device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__ XV, const SvdSec& s, const BjSec& b,
+                        int si, int pi, int round, float* __restrict__ W, float* __restrict__ V, float tol,
+                        float noise_c, float* __restrict__ gmax, int inner_sweeps) {
+    int cI, kI, cJ, kJ;
+    if (b.nb == 1) {
+        if (round != 0) return false;
+        cI = 0; kI = s.n; cJ = 0; kJ = 0;
+    } else {
+        if (round >= b.nbp - 1) return false;
+        int I = rr_pos(pi, round, b.nbp), J = rr_pos(b.nbp - 1 - pi, round, b.nbp);
+        if (I > J) { const int t = I; I = J; J = t; }
+        if (J >= b.nb) return false;
+        cI = I * BJ_B; kI = min(BJ_B, s.n - cI);
+        cJ = J * BJ_B; kJ = min(BJ_B, s.n - cJ);
+    }
+    const int k = kI + kJ;
+    const int tid = threadIdx.x;
+    const bool split = XV != XW;
+    if (tid < BJ_K) S.gcol[tid] = tid < kI ? cI + tid : (tid < k ? cJ + tid - kI : -1);
+    __syncthreads();
+    bj_stage_async(XW, W + s.w_off, s.p, S.gcol);
+    cp_async_commit();
+    if (split) bj_stage_async(XV, V + s.v_off, s.n, S.gcol);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    bj_gram(S, XW, s.p);
+    __syncthreads();
+    if (tid < 32) {
+        float d = tid < k ? S.G[tid * BJ_LD + tid] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+        if (tid == 0) {
+            float g = *((volatile float*)&gmax[si]);
+            if (d > g) {
+                atomicMax(reinterpret_cast<int*>(&gmax[si]), __float_as_int(d));
+                g = d;
+            }
+            S.noise = noise_c * sqrtf(g);
+        }
+    }
+    __syncthreads();
+    const float noise = S.noise;
+    int need = 0;
+    for (int e = tid; e < BJ_K * BJ_K; e += BJ_THREADS) {
+        const int u = e >> 5, v = e & 31;
+        if (u < v && v < k)
+            need |= bj_need(S.G[u * BJ_LD + v], S.G[u * BJ_LD + u], S.G[v * BJ_LD + v], tol, noise);
+    }
+    if (!__syncthreads_or(need)) {
+        cp_async_wait<0>();
+        __syncthreads();
+        return false;
+    }
+    bj_inner(S, inner_sweeps, tol, noise);
+    // order the eigenvectors by decreasing eigenvalue (ties: lower index first)
+    if (tid < BJ_K) S.diag[tid] = S.G[tid * BJ_LD + tid];
+    __syncthreads();
+    if (tid < BJ_K) {
+        const float d = S.diag[tid];
+        int r = 0;
+        for (int v = 0; v < BJ_K; ++v) r += (S.diag[v] > d) || (S.diag[v] == d && v < tid);
+        S.perm[r] = tid;
+    }
+    __syncthreads();
+    float* Qp = S.Q[1];
+    for (int e = tid; e < BJ_K * BJ_K; e += BJ_THREADS) {
+        const int u = e >> 5, r = e & 31;
+        Qp[u * BJ_QLD + r] = S.Q[0][u * BJ_QLD + S.perm[r]];
+    }
+    __syncthreads();
+    bj_rotate(XW, Qp, s.p);
+    __syncthreads();
+    bj_unstage(XW, W + s.w_off, s.p, S.gcol, k);
+    if (!split) {
+        __syncthreads();
+        bj_stage_async(XV, V + s.v_off, s.n, S.gcol);
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    bj_rotate(XV, Qp, s.n);
+    __syncthreads();
+    bj_unstage(XV, V + s.v_off, s.n, S.gcol, k);
+    __syncthreads();
+    return true;
+}
+
+// All sweeps in one cooperative launch.  rot[sweep] counts the pairs rotated in that sweep
+// (zeroed by the host); *sweeps = sweeps run; gmax: per-sector largest squared column norm seen
+// (zeroed by the host); bar: 3 zeroed words for the barrier.
+__global__ void __launch_bounds__(BJ_THREADS, 1)
+    k_bjacobi(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
+              int ntasks, int nrounds, int max_sweeps, int inner_sweeps, int max_p, int split, float* __restrict__ W,
+              float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax, int* __restrict__ rot,
+              int* __restrict__ sweeps, unsigned* __restrict__ bar, unsigned* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char bj_smem[];
+    BjShared& S = *reinterpret_cast<BjShared*>(bj_smem);
+    float* XW = reinterpret_cast<float*>(bj_smem + sizeof(BjShared));
+    float* XV = split ? XW + (size_t)max_p * BJ_LD : XW;
+    for (int e = threadIdx.x; e < (BJ_K - 1) * BJ_NP; e += blockDim.x) {
+        const int rnd = e / BJ_NP, i = e % BJ_NP;
+        const int a = rr_pos(i, rnd, BJ_K), b = rr_pos(BJ_K - 1 - i, rnd, BJ_K);
+        S.lo[rnd][i] = (unsigned char)min(a, b);
+        S.hi[rnd][i] = (unsigned char)max(a, b);
+    }
+    __syncthreads();
+    int done = 0;
+    bool alive = true;
+    while (done < max_sweeps && alive) {
+        const int sweep = done;
+        for (int round = 0; round < nrounds && alive; ++round) {
+            for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+                const int si = task_sec[t];
+                const SvdSec s = secs[si];
+                const BjSec b = bsecs[si];
+                if (bj_task(S, XW, XV, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax, inner_sweeps) &&
+                    threadIdx.x == 0)
+                    atomicAdd(&rot[sweep], 1);
+            }
+            alive = grid_barrier(bar, gridDim.x, err);
+        }
+        if (!alive) break;
+        ++done;
+        if (*((volatile int*)&rot[sweep]) == 0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = done;
+}
+
+}  // namespace
+
+int bjacobi_max_rows() { return (int)((BJ_SMEM_MAX - sizeof(BjShared)) / (BJ_LD * sizeof(float))); }
+
+void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
+                    int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c,
+                    float* gmax, int* rot, int* sweeps, unsigned* bar, unsigned* err, cudaStream_t st) {
+    if (ntasks <= 0 || nrounds <= 0) return;
+    PD_REQUIRE(max_rows <= bjacobi_max_rows(), DMRG_ERR_CAPACITY, "block Jacobi: sector rows exceed shared memory");
+    max_rows = std::max(1, max_rows);
+    // W and V staged side by side when both fit (V then loads while W is processed)
+    const size_t row_bytes = BJ_LD * sizeof(float);
+    int split = sizeof(BjShared) + (size_t)(max_rows + max_n) * row_bytes <= (size_t)BJ_SMEM_MAX;
+    const size_t smem = sizeof(BjShared) + (size_t)(split ? max_rows + max_n : max_rows) * row_bytes;
+    PD_CK(cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, BJ_THREADS, smem));
+    PD_REQUIRE(per_sm > 0, DMRG_ERR_CAPACITY, "block Jacobi: kernel does not fit on an SM");
+    PD_CK(cudaGetDevice(&dev));
+    PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = std::max(1, std::min(ntasks, per_sm * sms));
+    PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+    void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&task_sec, (void*)&ntasks, (void*)&nrounds,
+                    (void*)&max_sweeps, (void*)&inner_sweeps, (void*)&max_rows, (void*)&split, (void*)&W, (void*)&V, (void*)&tol,
+                    (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps, (void*)&bar, (void*)&err};
+    PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi, blocks, BJ_THREADS, args, smem, st));
+    PD_LAUNCHED();
+}
+
+}  // namespace pd

@@ -180,12 +180,22 @@ template <class T>
 void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, T* V, cudaStream_t st);
 // All Jacobi sweeps (until a sweep without rotation, at most max_sweeps) in one cooperative launch.
 // Pairs whose smaller column norm is below eta * |W_sector|_F are not rotated (eta = 0: all are).
-// floor2: nsec doubles of scratch.
+// floor2: nsec doubles of scratch (unused when eta = 0).
 // bar: 3 unsigned words of scratch for the bounded grid barrier; err: device error word.
 template <class T>
 void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs, int maxnpad, int max_sweeps, T* W,
                    T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, unsigned* bar, unsigned* err,
                    cudaStream_t st);
+// Block one-sided Jacobi (FP32, blocks of 16 columns) over the same sector batch.  Per sector:
+// nb = ceil(n / 16) blocks, nbp = nb rounded up to even, task0 = first task of the sector in a
+// round, ntask = tasks per round (nbp / 2; 1 when nb = 1).  task_sec[t] = sector of task t.
+struct BjSec {
+    int nb, nbp, task0, ntask;
+};
+int bjacobi_max_rows();
+void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
+                    int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c, float* gmax,
+                    int* rot, int* sweeps, unsigned* bar, unsigned* err, cudaStream_t st);
 template <class T>
 void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st);
 

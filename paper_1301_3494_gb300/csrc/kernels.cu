@@ -11,6 +11,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "grid_sync.cuh"
 #include "internal.h"
 
 
@@ -423,45 +424,6 @@ __device__ __forceinline__ bool jacobi_pair(const SvdSec& s, int pi, int round, 
     return true;
 }
 
-// Grid-wide barrier with a time bound (the launch is cooperative, so all blocks are resident).
-// bar[0] = arrival count, bar[1] = generation, bar[2] = abort flag.  On expiry the block sets
-// ERRBIT_TIMEOUT and the abort flag, and every later barrier returns false at once.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vbar = bar;
-        int ok = vbar[2] == 0u;
-        if (ok) {
-            const unsigned gen = vbar[1];
-            __threadfence();
-            if (atomicAdd(&bar[0], 1u) == nblocks - 1u) {
-                atomicExch(&bar[0], 0u);
-                __threadfence();
-                atomicAdd(&bar[1], 1u);
-            } else {
-                uint64_t t0;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-                while (vbar[1] == gen) {
-                    if (vbar[2]) { ok = 0; break; }
-                    uint64_t t;
-                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                    if (t - t0 > 2000000000ull) {
-                        atomicOr(err, ERRBIT_TIMEOUT);
-                        atomicExch(&bar[2], 1u);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-        }
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
 // All sweeps of all sectors in one cooperative launch; bounded grid barrier between rounds.
 // rot[sweep] counts the warps that rotated in that sweep (zeroed by the host); *sweeps = sweeps
 // run; bar: 3 zeroed words for the barrier.
@@ -481,7 +443,7 @@ __global__ void k_jacobi_coop(const SvdSec* __restrict__ secs, const int* __rest
             for (int w = gw; w < npairs; w += nw) {
                 const int si = pair_sec[w];
                 const SvdSec s = secs[si];
-                if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, (T)floor2[si], lane)) mine = 1;
+                if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, floor2 ? (T)floor2[si] : T(0), lane)) mine = 1;
             }
             alive = grid_barrier(bar, gridDim.x, err);
         }
@@ -745,8 +707,12 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
                    T* V, T tol, double eta, double* floor2, int* rot, int* sweeps, unsigned* bar, unsigned* err,
                    cudaStream_t st) {
     if (npairs <= 0 || maxnpad < 2) return;
-    k_svd_floor<T><<<nsec, 256, 0, st>>>(secs, W, eta, floor2);
-    PD_LAUNCHED();
+    const double* fl = nullptr;
+    if (eta > 0.0) {
+        k_svd_floor<T><<<nsec, 256, 0, st>>>(secs, W, eta, floor2);
+        PD_LAUNCHED();
+        fl = floor2;
+    }
     const int threads = 128;   // register-heavy pair updates: small blocks keep several per SM
     static int per_sm[2] = {0, 0};
     int& ps = per_sm[sizeof(T) == 8 ? 1 : 0];
@@ -756,7 +722,6 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
     PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int need = (npairs * 32 + threads - 1) / threads;
     int blocks = std::max(1, std::min(need, ps * sms));
-    const double* fl = floor2;
     PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
     void* args[] = {(void*)&secs, (void*)&pair_sec, (void*)&npairs, (void*)&maxnpad, (void*)&max_sweeps,
                     (void*)&W, (void*)&V, (void*)&tol, (void*)&fl, (void*)&rot, (void*)&sweeps, (void*)&bar,

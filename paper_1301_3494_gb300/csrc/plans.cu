@@ -1123,9 +1123,34 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it; the
         // kept factor that joins a block is re-orthonormalised in FP64 afterwards
         const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)maxp));
-        launch_jacobi<float>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, 40, dW.as<float>(),
-                             dV.as<float>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(), drot.as<int>() + max_sweeps,
-                             bar, jerr, st);
+        if (maxp <= bjacobi_max_rows()) {
+            // block Jacobi: one task per block pair, n / 16 - 1 rounds per sweep
+            std::vector<BjSec> bs(nsec);
+            std::vector<int> task_sec;
+            int nrounds = 0;
+            for (int s = 0; s < nsec; ++s) {
+                BjSec b{};
+                b.nb = (ss[s].n + 15) / 16;
+                b.nbp = b.nb + (b.nb & 1);
+                b.task0 = (int)task_sec.size();
+                b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
+                for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
+                if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
+                bs[s] = b;
+            }
+            DBuf dbs, dts, dgmax;
+            upload(dbs, bs, st);
+            upload(dts, task_sec, st);
+            dgmax.ensure(std::max(1, nsec) * 4, st);
+            PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
+            launch_bjacobi(dsecs.as<SvdSec>(), dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, maxp, maxn, 40,
+                           2, dW.as<float>(), dV.as<float>(), tol, 8.0f * FLT_EPSILON, dgmax.as<float>(),
+                           drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr, st);
+        } else {
+            launch_jacobi<float>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, 40, dW.as<float>(),
+                                 dV.as<float>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(),
+                                 drot.as<int>() + max_sweeps, bar, jerr, st);
+        }
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
         run_copy<double>(gather, psi, dW.p, Num::F64, st);

@@ -124,6 +124,56 @@ def test_svd_split_matches_oracle(kind, m, mmax):
         assert np.abs(rec_g[k] - rec_o[k]).max() <= 1e-11, k
 
 
+@pytest.mark.parametrize("kind,m,mmax", [("chain", 200, 120), ("cyl", 160, 90), ("cyl", 420, 300), ("tfim", 80, 50)])
+def test_svd_split_fp32_block_jacobi(kind, m, mmax):
+    """Mixed-precision split (FP32 block Jacobi, A re-orthonormalised in FP64) against the FP64
+    oracle.  FP32 columns carry absolute errors ~eps_f32 * lambda_max and pairs stop rotating at a
+    relative off-diagonal of 3e-5, so singular values agree to 1e-4 * lambda_max and the
+    reconstruction to 2e-4 normwise; A is orthonormal to FP64
+    accuracy; the block table equals the oracle's wherever the cut has a gap above that error."""
+    mpo, qn, bl, br, _, j, rng = _bond_case(kind, m, 3)
+    psi = {}
+    for k in LY.psi_keys(bl, br, qn):
+        a, c = bl[k[0]], br[k[0] + qn[k[1]] + qn[k[2]]]
+        psi[k] = rng.standard_normal((a, c)) * np.exp(-0.02 * np.add.outer(np.arange(a), np.arange(c)))
+    nrm = np.sqrt(sum((v ** 2).sum() for v in psi.values()))
+    psi = {k: v / nrm for k, v in psi.items()}
+    A, lam, B, counts, err = O.split_two_site(psi, bl, br, qn, mmax)
+    lam_all = np.sort(np.concatenate(list(lam.values())))[::-1]
+    bond = pd.Bond(qn, bl, br, mpo.W[j], mpo.flux[j], mpo.flux[j + 1])
+    x = _dev(LY.pack_psi(psi, bl, br, qn))
+    n = x.numel()
+    Ad = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+    Bd = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+    ld = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+    mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, 2, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
+    torch.cuda.synchronize()
+    # the oracle's full spectrum decides whether the cut is resolvable in FP32
+    full = O.split_two_site(psi, bl, br, qn, 10 ** 9)[1]
+    spec = np.sort(np.concatenate(list(full.values())))[::-1]
+    kept = int(sum(mid.values()))
+    if len(spec) > mmax and spec[mmax - 1] - spec[mmax] > 1e-4 * spec[0] and spec[mmax - 1] > 1e-4 * spec[0]:
+        assert mid == counts
+    assert kept <= mmax
+    lam_gpu = ld.cpu().numpy()[:kept]
+    got = np.sort(lam_gpu)[::-1]
+    assert np.abs(got - spec[:kept] / np.sqrt((spec[:kept] ** 2).sum())).max() <= 1e-4 * spec[0]
+    Ag = LY.unpack_site(Ad.cpu().numpy(), bl, mid, qn)
+    Bg = LY.unpack_site(Bd.cpu().numpy(), mid, br, qn)
+    for q in mid:   # A^T A = 1 per middle sector, FP64 accuracy
+        cols = [v for k, v in Ag.items() if k[0] + qn[k[1]] == q]
+        M = np.concatenate(cols, axis=0)
+        assert np.abs(M.T @ M - np.eye(M.shape[1])).max() <= 1e-12
+    lg, off = {}, 0
+    for q in sorted(mid):
+        lg[q] = lam_gpu[off: off + mid[q]]
+        off += mid[q]
+    rec_g = O.two_site({k: v * lg[k[0] + qn[k[1]]][None, :] for k, v in Ag.items()}, Bg, qn)
+    rec_o = O.two_site({k: v * lam[k[0] + qn[k[1]]][None, :] for k, v in A.items()}, B, qn)
+    diff = sum(((rec_g.get(k, 0) - rec_o[k]) ** 2).sum() for k in rec_o)
+    assert np.sqrt(diff) <= 2e-4 + 2 * np.sqrt(err)
+
+
 # ------------------------------------------------------------------------------------------
 # Tensor-core (tcgen05) paths: normwise relative error against the FP64 oracle.  Bounds from
 # the operand rounding: bf16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3; psi, L, R and
