@@ -1040,11 +1040,210 @@ void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     *lam_elems = l;
 }
 
+namespace {
+
+// Column copy: dst[dst + r] = scale * src[src + r] for r < rows, scale = 1 / sig[sig_idx] (0 when
+// that value is 0) if sig_idx >= 0, else 1.  One CTA per column.
+struct ColJob {
+    long long src, dst, sig_idx;
+    int rows, pad_;
+};
+__global__ void k_col_copy(const ColJob* __restrict__ jobs, const double* __restrict__ src, double* __restrict__ dst,
+                           const double* __restrict__ sig) {
+    const ColJob j = jobs[blockIdx.x];
+    double sc = 1.0;
+    if (j.sig_idx >= 0) {
+        const double v = sig[j.sig_idx];
+        sc = v > 0.0 ? 1.0 / v : 0.0;
+    }
+    for (int r = threadIdx.x; r < j.rows; r += blockDim.x) dst[j.dst + r] = sc * src[j.src + r];
+}
+
+void col_copy(const std::vector<ColJob>& jobs, const double* src, double* dst, const double* sig, cudaStream_t st) {
+    if (jobs.empty()) return;
+    DBuf dj;
+    upload(dj, jobs, st);
+    k_col_copy<<<(unsigned)jobs.size(), 128, 0, st>>>(dj.as<ColJob>(), src, dst, sig);
+    PD_LAUNCHED();
+}
+
+// FP64 one-sided Jacobi SVD of the column-major matrices W_s (p_s x n_s, n_s <= p_s) at ss[s].w_off
+// of W (overwritten by U_s Sigma_s).  Fills v_off / s_off / npad / pair0 of ss; V receives V_s,
+// sig the column norms and ord their descending order; dsecs the device copy of ss.
+void jacobi64(std::vector<SvdSec>& ss, double* W, DBuf& dsecs, DBuf& dV, DBuf& dsig, DBuf& dord, cudaStream_t st) {
+    const int nsec = (int)ss.size();
+    std::vector<int> pair_sec;
+    long long voff = 0, soff = 0;
+    int maxn = 0, maxnpad = 0, maxp = 1;
+    for (int s = 0; s < nsec; ++s) {
+        SvdSec& x = ss[s];
+        x.npad = x.n + (x.n & 1);
+        x.v_off = voff;
+        x.s_off = soff;
+        x.pair0 = (int)pair_sec.size();
+        for (int i = 0; i < x.npad / 2; ++i) pair_sec.push_back(s);
+        voff += (long long)x.n * x.n;
+        soff += x.n;
+        maxn = std::max(maxn, x.n);
+        maxp = std::max(maxp, x.p);
+        maxnpad = std::max(maxnpad, x.npad);
+    }
+    const int max_sweeps = 60;
+    DBuf dpairs, drot, dbar;
+    upload(dsecs, ss, st);
+    upload(dpairs, pair_sec, st);
+    dV.ensure(std::max<long long>(1, voff) * 8, st);
+    dsig.ensure(std::max<long long>(1, soff) * 8, st);
+    dord.ensure(std::max<long long>(1, soff) * 4, st);
+    drot.ensure((max_sweeps + 1) * 4, st);
+    dbar.ensure(4 * sizeof(unsigned), st);
+    PD_CK(cudaMemsetAsync(drot.p, 0, (max_sweeps + 1) * 4, st));
+    PD_CK(cudaMemsetAsync(dbar.p, 0, 4 * sizeof(unsigned), st));
+    unsigned* bar = dbar.as<unsigned>();
+    launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
+    const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+    launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), (int)pair_sec.size(), maxnpad, max_sweeps, W,
+                          dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(), drot.as<int>() + max_sweeps, bar, bar + 3,
+                          st);
+    launch_svd_finish<double>(dsecs.as<SvdSec>(), nsec, W, dsig.as<double>(), dord.as<int>(), st);
+    unsigned err = 0;
+    PD_CK(cudaMemcpyAsync(&err, bar + 3, 4, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    PD_REQUIRE(!(err & ERRBIT_TIMEOUT), DMRG_ERR_TIMEOUT, "Jacobi SVD grid barrier timed out");
+}
+
+// The Appendix's accurate SVD, applied to a finished batch (W = U Sigma, V, sig, ord; M the
+// matrices the SVD was taken of, same layout as W).  Per matrix, with singular values
+// lambda_1 >= ... >= lambda_n: p = the first index with lambda_p / lambda_1 < eps; if there is one,
+// X = U_p^T M V_p over the columns p..n, the same SVD and refinement recursively on X, then
+// U_p <- U_p U_X, V_p <- V_p V_X, lambda_p.. <- lambda_X.  Results written back into W, V, and
+// sig / ord recomputed.
+constexpr double ACC_EPS = 1e-4;
+void accurate_refine(const std::vector<SvdSec>& ss, const SvdSec* dsecs, double* W, double* V, double* sig, int* ord,
+                     const double* M, int depth, cudaStream_t st) {
+    const int nsec = (int)ss.size();
+    long long total = 0;
+    for (const auto& x : ss) total = std::max(total, x.s_off + x.n);
+    if (total == 0) return;
+    std::vector<double> hsig(total);
+    std::vector<int> hord(total);
+    PD_CK(cudaMemcpyAsync(hsig.data(), sig, total * 8, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(hord.data(), ord, total * 4, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    struct Ref {
+        int s, p, q;
+        long long up, vp, x;
+    };
+    std::vector<Ref> refs;
+    long long nup = 0, nvp = 0, nx = 0;
+    for (int s = 0; s < nsec; ++s) {
+        const SvdSec& S = ss[s];
+        if (S.n <= 1) continue;
+        const double l0 = hsig[S.s_off + hord[S.s_off]];
+        if (!(l0 > 0.0)) continue;
+        int p = -1;
+        for (int i = 1; i < S.n; ++i)
+            if (hsig[S.s_off + hord[S.s_off + i]] / l0 < ACC_EPS) {
+                p = i;
+                break;
+            }
+        if (p < 0) continue;
+        const int q = S.n - p;
+        refs.push_back({s, p, q, nup, nvp, nx});
+        nup += (long long)S.p * q;
+        nvp += (long long)S.n * q;
+        nx += (long long)q * q;
+    }
+    if (refs.empty()) return;
+    PD_REQUIRE(depth < 64, DMRG_ERR_NUMERIC, "accurate SVD recursion did not terminate");
+    DBuf dUp, dVp, dT, dX;
+    dUp.ensure(nup * 8, st);
+    dVp.ensure(nvp * 8, st);
+    dT.ensure(nup * 8, st);
+    dX.ensure(nx * 8, st);
+    // U_p (normalised columns of W in descending order from p) and V_p
+    std::vector<ColJob> gu, gv;
+    for (const auto& r : refs) {
+        const SvdSec& S = ss[r.s];
+        for (int j = 0; j < r.q; ++j) {
+            const int c = hord[S.s_off + r.p + j];
+            gu.push_back({S.w_off + (long long)c * S.p, r.up + (long long)j * S.p, S.s_off + c, S.p, 0});
+            gv.push_back({S.v_off + (long long)c * S.n, r.vp + (long long)j * S.n, -1, S.n, 0});
+        }
+    }
+    col_copy(gu, W, dUp.as<double>(), sig, st);
+    col_copy(gv, V, dVp.as<double>(), nullptr, st);
+    // T = M V_p (p x q), X = U_p^T T (q x q)
+    GemmBatch g1, g2;
+    for (const auto& r : refs) {
+        const SvdSec& S = ss[r.s];
+        g1.add(S.p, r.q, r.up, 1, S.p, S.n, 1, 1, S.p, {GSeg{S.w_off, r.vp, S.n, 0}});
+        g2.add(r.q, r.q, r.x, S.p, 1, S.p, 1, 1, r.q, {GSeg{r.up, r.up, S.p, 0}});
+    }
+    run_gemm64(g1, M, dVp.as<double>(), dT.as<double>(), st);
+    run_gemm64(g2, dUp.as<double>(), dT.as<double>(), dX.as<double>(), st);
+    // the same SVD and refinement of X
+    std::vector<SvdSec> xs(refs.size());
+    for (size_t i = 0; i < refs.size(); ++i) {
+        xs[i] = SvdSec{};
+        xs[i].w_off = refs[i].x;
+        xs[i].p = xs[i].n = refs[i].q;
+    }
+    DBuf dXW, dXsecs, dXV, dXsig, dXord;
+    dXW.ensure(nx * 8, st);
+    PD_CK(cudaMemcpyAsync(dXW.p, dX.p, nx * 8, cudaMemcpyDeviceToDevice, st));
+    jacobi64(xs, dXW.as<double>(), dXsecs, dXV, dXsig, dXord, st);
+    accurate_refine(xs, dXsecs.as<SvdSec>(), dXW.as<double>(), dXV.as<double>(), dXsig.as<double>(),
+                    dXord.as<int>(), dX.as<double>(), depth + 1, st);
+    std::vector<int> hxo(nx > 0 ? (size_t)std::max<long long>(1, xs.back().s_off + xs.back().n) : 1);
+    PD_CK(cudaMemcpyAsync(hxo.data(), dXord.p, hxo.size() * 4, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    // X factors with columns in descending order (W_X keeps U_X Sigma_X)
+    DBuf dWxp, dVxp;
+    dWxp.ensure(nx * 8, st);
+    dVxp.ensure(nx * 8, st);
+    std::vector<ColJob> gw, gx;
+    for (size_t i = 0; i < refs.size(); ++i) {
+        const int q = refs[i].q;
+        for (int j = 0; j < q; ++j) {
+            const int c = hxo[xs[i].s_off + j];
+            gw.push_back({xs[i].w_off + (long long)c * q, refs[i].x + (long long)j * q, -1, q, 0});
+            gx.push_back({xs[i].v_off + (long long)c * q, refs[i].x + (long long)j * q, -1, q, 0});
+        }
+    }
+    col_copy(gw, dXW.as<double>(), dWxp.as<double>(), nullptr, st);
+    col_copy(gx, dXV.as<double>(), dVxp.as<double>(), nullptr, st);
+    // new columns: U_p (U_X Sigma_X) into T, V_p V_X into Vn
+    DBuf dVn;
+    dVn.ensure(nvp * 8, st);
+    GemmBatch g3, g4;
+    for (const auto& r : refs) {
+        const SvdSec& S = ss[r.s];
+        g3.add(S.p, r.q, r.up, 1, S.p, r.q, 1, 1, S.p, {GSeg{r.up, r.x, r.q, 0}});
+        g4.add(S.n, r.q, r.vp, 1, S.n, r.q, 1, 1, S.n, {GSeg{r.vp, r.x, r.q, 0}});
+    }
+    run_gemm64(g3, dUp.as<double>(), dWxp.as<double>(), dT.as<double>(), st);
+    run_gemm64(g4, dVp.as<double>(), dVxp.as<double>(), dVn.as<double>(), st);
+    std::vector<ColJob> sw, sv;
+    for (const auto& r : refs) {
+        const SvdSec& S = ss[r.s];
+        for (int j = 0; j < r.q; ++j) {
+            const int c = hord[S.s_off + r.p + j];
+            sw.push_back({r.up + (long long)j * S.p, S.w_off + (long long)c * S.p, -1, S.p, 0});
+            sv.push_back({r.vp + (long long)j * S.n, S.v_off + (long long)c * S.n, -1, S.n, 0});
+        }
+    }
+    col_copy(sw, dT.as<double>(), W, nullptr, st);
+    col_copy(sv, dVn.as<double>(), V, nullptr, st);
+    launch_svd_finish<double>(dsecs, nsec, W, sig, ord, st);
+}
+
+}  // namespace
+
 SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
                       const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
                       int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st,
                       bool fp32) {
-    (void)accurate;
     const size_t es = fp32 ? 4 : 8;
     const PsiLayout P = psi_layout2(bl, br, qn1, qn2);
     const std::vector<int>& qn = qn1;
@@ -1154,12 +1353,20 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
         run_copy<double>(gather, psi, dW.p, Num::F64, st);
+        DBuf dM;
+        if (accurate && woff > 0) {
+            dM.ensure(woff * 8, st);
+            PD_CK(cudaMemcpyAsync(dM.p, dW.p, woff * 8, cudaMemcpyDeviceToDevice, st));
+        }
         launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
         const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
         launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps,
-                              dW.as<double>(), dV.as<double>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(),
+                              dW.as<double>(), dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(),
                               drot.as<int>() + max_sweeps, bar, jerr, st);
         launch_svd_finish<double>(dsecs.as<SvdSec>(), nsec, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
+        if (accurate && woff > 0)
+            accurate_refine(ss, dsecs.as<SvdSec>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(),
+                            dord.as<int>(), dM.as<double>(), 0, st);
     }
     if (sv0) {
         PD_CK(cudaEventRecord(sv1, st));
