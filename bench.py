@@ -56,6 +56,9 @@ def parse():
                          "steps: a step is one bulk two-site update (serial); op: repeated H_eff matvecs at "
                          "one bond (random environments, small device footprint, for profiler captures)")
     ap.add_argument("--regions", type=int, default=4)
+    ap.add_argument("--concurrent-regions", action="store_true",
+                    help="sweeps: one host thread and stream per region, overlapping on the GPU (default: the "
+                         "regions run one after another, each with the whole GPU)")
     return ap.parse_args()
 
 
@@ -316,6 +319,7 @@ def main():
     # a fixed number of Davidson steps: tensor-core iterations, then an FP32-accurate refinement
     dav = dict(dav_tol=0.0, dav_max_iter=args.dav_iters, refine_iters=args.refine_iters)
     if args.mode == "sweeps":
+        dav["serial_regions"] = 0 if args.concurrent_regions else 1
         eng.setup_regions(args.regions, 0, args.m, **dav)
         run_step = lambda: eng.sweep(args.m, **dav)
     else:
@@ -378,6 +382,8 @@ def main():
                    "m": args.m, "sectors_at_centre": len(mps.bonds[L // 2]), "step": args.mode,
                    "dav_iters": args.dav_iters, "refine_iters": args.refine_iters, "kmax": args.kmax,
                    "precision": args.precision, "regions": args.regions if args.mode == "sweeps" else 1,
+                   "region_schedule": (("concurrent" if args.concurrent_regions else "serial")
+                                       if args.mode == "sweeps" else None),
                    "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
                    "setup_s": t_setup},
         "sweep_s": ms_step / 1e3 if args.mode == "sweeps" else ms_step * 2 * (L - 1) / 1e3,
@@ -395,7 +401,10 @@ def main():
                 "h2d_bytes_per_step": ctypes.sizeof(pd.SweepParams),
                 "d2h_bytes_per_step": ctypes.sizeof(pd.SweepStats)},
         "svd": {"calls": prof["svd_calls"], "sweeps_per_call": prof["svd_sweeps"] / max(1, prof["svd_calls"]),
-                "ms_per_call": prof["svd_ms"] / max(1, prof["svd_calls"])},
+                "ms_per_call": prof["svd_ms"] / max(1, prof["svd_calls"]),
+                "block_calls": prof["svd_block_calls"], "block_ms": prof["svd_block_ms"],
+                "fp64_calls": prof["svd_fp64_calls"], "fp64_ms": prof["svd_fp64_ms"],
+                "max_sector_rows": prof["svd_max_rows"], "fp64_fallbacks": prof["svd_fp64_fallbacks"]},
         "env_update_ms_per_step": prof["f32_gemm_ms"] / args.steps if args.precision != "fp64" else None,
         "gpu_launches": prof["launches"],
         "clocks": clocks,

@@ -104,6 +104,11 @@ typedef struct {
                                mixed modes)                                                   */
     int refine_iters;       /* mixed modes only: Davidson iterations continued from the Ritz
                                vector with an FP32-accurate matvec (0 = none)                 */
+    int serial_regions;     /* region mode: 0 = one host thread and stream per region, the
+                               regions' work overlapping on the GPU; 1 = the calling thread
+                               runs the regions one after another (each gets the whole GPU;
+                               the same results, since regions are independent between
+                               merges)                                                        */
 } dmrg_sweep_params;
 
 typedef struct {
@@ -213,6 +218,12 @@ typedef struct {
     long long svd_calls;         /* block-sparse SVDs (one per two-site split)                  */
     long long svd_sweeps;        /* Jacobi sweeps they ran in total                             */
     double svd_ms;               /* device time of their Jacobi kernels                         */
+    long long svd_block_calls;   /* of those, FP32 splits run by the block Jacobi                */
+    long long svd_fp64_calls;    /* of those, FP64 splits (parity mode, shared bonds)            */
+    double svd_block_ms;         /* device time of the block-Jacobi splits                      */
+    double svd_fp64_ms;          /* device time of the FP64 splits                              */
+    long long svd_max_rows;      /* largest sector row count seen                               */
+    long long svd_fp64_fallbacks; /* FP32 splits redone in FP64 (re-orthonormalisation refused)  */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);

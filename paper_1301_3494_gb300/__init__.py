@@ -40,7 +40,9 @@ class Profile(C.Structure):
                 ("env_gemm_flops", C.c_double), ("f64_gemm_launches", C.c_longlong), ("f64_gemm_ms", C.c_double),
                 ("f64_gemm_flops", C.c_double), ("f32_gemm_launches", C.c_longlong), ("f32_gemm_ms", C.c_double),
                 ("f32_gemm_flops", C.c_double), ("svd_calls", C.c_longlong), ("svd_sweeps", C.c_longlong),
-                ("svd_ms", C.c_double)]
+                ("svd_ms", C.c_double), ("svd_block_calls", C.c_longlong), ("svd_fp64_calls", C.c_longlong),
+                ("svd_block_ms", C.c_double), ("svd_fp64_ms", C.c_double), ("svd_max_rows", C.c_longlong),
+                ("svd_fp64_fallbacks", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -51,7 +53,8 @@ class Config(C.Structure):
 
 
 class SweepParams(C.Structure):
-    _fields_ = [("m_max", C.c_int), ("dav_tol", C.c_double), ("dav_max_iter", C.c_int), ("refine_iters", C.c_int)]
+    _fields_ = [("m_max", C.c_int), ("dav_tol", C.c_double), ("dav_max_iter", C.c_int), ("refine_iters", C.c_int),
+                ("serial_regions", C.c_int)]
 
 
 class SweepStats(C.Structure):
@@ -236,8 +239,8 @@ class Engine:
         self._h = h
 
     @staticmethod
-    def params(m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
-        return SweepParams(int(m_max), float(dav_tol), int(dav_max_iter), int(refine_iters))
+    def params(m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2, serial_regions=0):
+        return SweepParams(int(m_max), float(dav_tol), int(dav_max_iter), int(refine_iters), int(serial_regions))
 
     def set_mps(self, bonds, site_data, center=None):
         """bonds: list of L+1 dicts charge -> dim; site_data: concatenated packed site tensors.
@@ -251,12 +254,13 @@ class Engine:
                        0 if center is None else 1, 0 if center is None else int(center))
         _check(lib().dmrg_set_mps(self._h, C.byref(desc)), self._h)
 
-    def setup_regions(self, n_regions, warmup, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
-        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters)
+    def setup_regions(self, n_regions, warmup, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2,
+                      serial_regions=0):
+        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters, serial_regions)
         _check(lib().dmrg_setup_regions(self._h, int(n_regions), int(warmup), C.byref(p)), self._h)
 
-    def sweep(self, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2):
-        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters)
+    def sweep(self, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2, serial_regions=0):
+        p = self.params(m_max, dav_tol, dav_max_iter, refine_iters, serial_regions)
         s = SweepStats()
         _check(lib().dmrg_sweep(self._h, C.byref(p), C.byref(s)), self._h)
         return s.as_dict()

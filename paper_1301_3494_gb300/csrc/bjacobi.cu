@@ -3,8 +3,10 @@
 //
 // The columns of every sector matrix W (p x n, column-major, n <= p) are cut into blocks of 16.
 // A sweep pairs every block with every other block once (round-robin ordering of the blocks);
-// a round processes all pairs of all sectors at once, one pair per CTA, and ends in a bounded
-// grid barrier.  For a pair (I, J), I < J, the CTA stages the p x 32 columns in shared memory,
+// a round processes all pairs of all sectors at once, one pair per CTA.  With the GPU to itself
+// the caller runs all sweeps in one cooperative launch (a bounded grid barrier ends each round);
+// while regions run concurrently, each round is its own launch (kernel boundaries order the
+// rounds and nothing spins, so the regions' kernels interleave freely).  For a pair (I, J), I < J, the CTA stages the p x 32 columns in shared memory,
 // forms their 32 x 32 Gram matrix, diagonalises it with a few sweeps of two-sided cyclic
 // Jacobi, orders the eigenvectors by decreasing eigenvalue (block I receives the larger ones),
 // and rotates the staged columns and the matching columns of V by that orthogonal matrix.  The
@@ -22,6 +24,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <vector>
 
 #include "grid_sync.cuh"
 #include "internal.h"
@@ -37,7 +40,7 @@ constexpr int BJ_LD = BJ_K + 1;              // row stride of staged rows (confl
 constexpr int BJ_QLD = BJ_K + 4;             // row stride of rotations (16-byte aligned rows)
 constexpr int BJ_THREADS = 256;
 constexpr int BJ_WARPS = BJ_THREADS / 32;
-constexpr int BJ_SMEM_MAX = 227 * 1024;
+constexpr int BJ_SMEM_MAX = 226 * 1024;        // dynamic shared memory ceiling (227 KB less static use)
 
 struct alignas(16) BjShared {
     float G[BJ_K * BJ_LD];             // Gram matrix (rotated in place)
@@ -71,14 +74,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// X[r][u] = src[gcol[u] * rows + r] (zero for padding columns), as asynchronous copies
-// (the caller commits and waits).
-__device__ __forceinline__ void bj_stage_async(float* __restrict__ X, const float* __restrict__ src, int rows,
-                                               const int* __restrict__ gcol) {
+// X[r][u] = src[gcol[u] * ld + r0 + r] for r < rows (zero for padding columns), as asynchronous
+// copies (the caller commits and waits).
+__device__ __forceinline__ void bj_stage_async(float* __restrict__ X, const float* __restrict__ src, int ld, int r0,
+                                               int rows, const int* __restrict__ gcol) {
     for (int u = 0; u < BJ_K; ++u) {
         const int c = gcol[u];
         if (c >= 0) {
-            const float* col = src + (long long)c * rows;
+            const float* col = src + (long long)c * ld + r0;
             for (int r = threadIdx.x; r < rows; r += BJ_THREADS) cp_async4(X + r * BJ_LD + u, col + r);
         } else {
             for (int r = threadIdx.x; r < rows; r += BJ_THREADS) X[r * BJ_LD + u] = 0.f;
@@ -86,10 +89,10 @@ __device__ __forceinline__ void bj_stage_async(float* __restrict__ X, const floa
     }
 }
 
-// dst[gcol[u] * rows + r] = X[r][u] for u < k: a thread reads a whole staged row, then stores
-// it to the k columns (coalesced across the warp).
-__device__ __forceinline__ void bj_unstage(const float* __restrict__ X, float* __restrict__ dst, int rows,
-                                           const int* __restrict__ gcol, int k) {
+// dst[gcol[u] * ld + r0 + r] = X[r][u] for u < k, r < rows: a thread reads a whole staged row,
+// then stores it to the k columns (coalesced across the warp).
+__device__ __forceinline__ void bj_unstage(const float* __restrict__ X, float* __restrict__ dst, int ld, int r0,
+                                           int rows, const int* __restrict__ gcol, int k) {
     int cols[BJ_K];
 #pragma unroll
     for (int u = 0; u < BJ_K; ++u) cols[u] = gcol[u];
@@ -99,20 +102,16 @@ __device__ __forceinline__ void bj_unstage(const float* __restrict__ X, float* _
         for (int u = 0; u < BJ_K; ++u) v[u] = X[r * BJ_LD + u];
 #pragma unroll
         for (int u = 0; u < BJ_K; ++u)
-            if (u < k) dst[(long long)cols[u] * rows + r] = v[u];
+            if (u < k) dst[(long long)cols[u] * ld + r0 + r] = v[u];
     }
 }
 
-// S.G = X^T X over `rows` staged rows.  Lane: an 8 x 8 tile of one of two interleaved row
-// halves of the warp's rows; halves summed by shuffle, warps summed in warp order.
-__device__ __forceinline__ void bj_gram(BjShared& S, const float* __restrict__ X, int rows) {
+// Gram accumulation over `rows` staged rows into a lane's 8 x 8 tile (one of two interleaved row
+// halves of the warp's rows); bj_gram_reduce then sums halves by shuffle and warps in warp order
+// into S.G.
+__device__ __forceinline__ void bj_gram_acc(float (&acc)[8][8], const float* __restrict__ X, int rows) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int u0 = 8 * (lane & 3), v0 = 8 * ((lane >> 2) & 3), half = lane >> 4;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     for (int r = 2 * w + half; r < rows; r += 2 * BJ_WARPS) {
         const float* xr = X + r * BJ_LD;
         float a[8], b[8];
@@ -125,6 +124,11 @@ __device__ __forceinline__ void bj_gram(BjShared& S, const float* __restrict__ X
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+}
+
+__device__ __forceinline__ void bj_gram_reduce(BjShared& S, float (&acc)[8][8]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u0 = 8 * (lane & 3), v0 = 8 * ((lane >> 2) & 3), half = lane >> 4;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -266,11 +270,31 @@ __device__ __forceinline__ void bj_inner(BjShared& S, int sweeps, float tol, flo
     }
 }
 
-// One block pair.  Returns true (in every thread) if it rotated.  XW: p staged rows; XV: n
-// staged rows (may alias XW, then V is staged after W has been written back).
-__device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__ XV, const SvdSec& s, const BjSec& b,
-                        int si, int pi, int round, float* __restrict__ W, float* __restrict__ V, float tol,
-                        float noise_c, float* __restrict__ gmax, int inner_sweeps) {
+// Rotate the k columns gcol of A (ld rows, `rows` of them) by Qp, staging at most `cap` rows at
+// a time in X.
+__device__ __forceinline__ void bj_rotate_streamed(float* __restrict__ X, float* __restrict__ A, int ld, int rows,
+                                                   int cap, const float* __restrict__ Qp, const int* __restrict__ gcol,
+                                                   int k) {
+    for (int r0 = 0; r0 < rows; r0 += cap) {
+        const int len = min(cap, rows - r0);
+        bj_stage_async(X, A, ld, r0, len, gcol);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        bj_rotate(X, Qp, len);
+        __syncthreads();
+        bj_unstage(X, A, ld, r0, len, gcol, k);
+        __syncthreads();
+    }
+}
+
+// One block pair.  Returns true (in every thread) if it rotated.  XW holds `cap` staged rows; XV
+// (n rows) is a separate area when `split` (V then loads while W is processed), else it aliases
+// XW.  A sector taller than cap is streamed through XW in row chunks (its W is read twice: once
+// for the Gram matrix, once for the rotation).
+__device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__ XV, int cap, const SvdSec& s,
+                        const BjSec& b, int si, int pi, int round, float* __restrict__ W, float* __restrict__ V,
+                        float tol, float noise_c, float* __restrict__ gmax, int inner_sweeps) {
     int cI, kI, cJ, kJ;
     if (b.nb == 1) {
         if (round != 0) return false;
@@ -285,16 +309,35 @@ __device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__
     }
     const int k = kI + kJ;
     const int tid = threadIdx.x;
-    const bool split = XV != XW;
+    const bool resident = s.p <= cap;                 // W's columns fit: staged once
+    const bool split = resident && XV != XW;          // and V's alongside
     if (tid < BJ_K) S.gcol[tid] = tid < kI ? cI + tid : (tid < k ? cJ + tid - kI : -1);
     __syncthreads();
-    bj_stage_async(XW, W + s.w_off, s.p, S.gcol);
-    cp_async_commit();
-    if (split) bj_stage_async(XV, V + s.v_off, s.n, S.gcol);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    bj_gram(S, XW, s.p);
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    if (resident) {
+        bj_stage_async(XW, W + s.w_off, s.p, 0, s.p, S.gcol);
+        cp_async_commit();
+        if (split) bj_stage_async(XV, V + s.v_off, s.n, 0, s.n, S.gcol);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        bj_gram_acc(acc, XW, s.p);
+    } else {
+        for (int r0 = 0; r0 < s.p; r0 += cap) {
+            const int len = min(cap, s.p - r0);
+            bj_stage_async(XW, W + s.w_off, s.p, r0, len, S.gcol);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            bj_gram_acc(acc, XW, len);
+            __syncthreads();
+        }
+    }
+    bj_gram_reduce(S, acc);
     __syncthreads();
     if (tid < 32) {
         float d = tid < k ? S.G[tid * BJ_LD + tid] : 0.f;
@@ -339,31 +382,66 @@ __device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__
         Qp[u * BJ_QLD + r] = S.Q[0][u * BJ_QLD + S.perm[r]];
     }
     __syncthreads();
-    bj_rotate(XW, Qp, s.p);
-    __syncthreads();
-    bj_unstage(XW, W + s.w_off, s.p, S.gcol, k);
-    if (!split) {
+    if (resident) {
+        bj_rotate(XW, Qp, s.p);
         __syncthreads();
-        bj_stage_async(XV, V + s.v_off, s.n, S.gcol);
-        cp_async_commit();
+        bj_unstage(XW, W + s.w_off, s.p, 0, s.p, S.gcol, k);
+        if (split) {
+            cp_async_wait<0>();
+            __syncthreads();
+            bj_rotate(XV, Qp, s.n);
+            __syncthreads();
+            bj_unstage(XV, V + s.v_off, s.n, 0, s.n, S.gcol, k);
+            __syncthreads();
+            return true;
+        }
+        __syncthreads();
+    } else {
+        bj_rotate_streamed(XW, W + s.w_off, s.p, s.p, cap, Qp, S.gcol, k);
     }
-    cp_async_wait<0>();
-    __syncthreads();
-    bj_rotate(XV, Qp, s.n);
-    __syncthreads();
-    bj_unstage(XV, V + s.v_off, s.n, S.gcol, k);
-    __syncthreads();
+    bj_rotate_streamed(XW, V + s.v_off, s.n, s.n, cap, Qp, S.gcol, k);
     return true;
 }
 
-// All sweeps in one cooperative launch.  rot[sweep] counts the pairs rotated in that sweep
-// (zeroed by the host); *sweeps = sweeps run; gmax: per-sector largest squared column norm seen
-// (zeroed by the host); bar: 3 zeroed words for the barrier.
+// One round of one sweep: every CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ...
+// rot[sweep] counts the pairs rotated in this sweep (zeroed by the host).  A launch whose previous
+// sweep rotated nothing returns at once (the host enqueues a sweep before it has read the result
+// of the one before).
 __global__ void __launch_bounds__(BJ_THREADS, 1)
-    k_bjacobi(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
-              int ntasks, int nrounds, int max_sweeps, int inner_sweeps, int max_p, int split, float* __restrict__ W,
-              float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax, int* __restrict__ rot,
-              int* __restrict__ sweeps, unsigned* __restrict__ bar, unsigned* __restrict__ err) {
+    k_bjacobi_round(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
+                    int ntasks, int round, int sweep, int inner_sweeps, int max_p, int split, float* __restrict__ W,
+                    float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax, int* __restrict__ rot) {
+    extern __shared__ __align__(16) unsigned char bj_smem[];
+    if (sweep > 0 && *((volatile int*)&rot[sweep - 1]) == 0) return;
+    BjShared& S = *reinterpret_cast<BjShared*>(bj_smem);
+    float* XW = reinterpret_cast<float*>(bj_smem + sizeof(BjShared));
+    float* XV = split ? XW + (size_t)max_p * BJ_LD : XW;
+    for (int e = threadIdx.x; e < (BJ_K - 1) * BJ_NP; e += blockDim.x) {
+        const int rnd = e / BJ_NP, i = e % BJ_NP;
+        const int a = rr_pos(i, rnd, BJ_K), b = rr_pos(BJ_K - 1 - i, rnd, BJ_K);
+        S.lo[rnd][i] = (unsigned char)min(a, b);
+        S.hi[rnd][i] = (unsigned char)max(a, b);
+    }
+    __syncthreads();
+    for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+        const int si = task_sec[t];
+        const SvdSec s = secs[si];
+        const BjSec b = bsecs[si];
+        if (bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax, inner_sweeps) &&
+            threadIdx.x == 0)
+            atomicAdd(&rot[sweep], 1);
+    }
+}
+
+// All sweeps in one cooperative launch, for a caller that has the GPU to itself: a bounded grid
+// barrier ends each round (cheaper than a kernel boundary).  rot[sweep] counts rotated pairs
+// (zeroed by the host); *sweeps = sweeps run; bar: 3 zeroed words for the barrier.
+__global__ void __launch_bounds__(BJ_THREADS, 1)
+    k_bjacobi_coop(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
+                   int ntasks, int nrounds, int max_sweeps, int inner_sweeps, int max_p, int split,
+                   float* __restrict__ W, float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax,
+                   int* __restrict__ rot, int* __restrict__ sweeps, unsigned* __restrict__ bar,
+                   unsigned* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     BjShared& S = *reinterpret_cast<BjShared*>(bj_smem);
     float* XW = reinterpret_cast<float*>(bj_smem + sizeof(BjShared));
@@ -384,7 +462,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
                 const int si = task_sec[t];
                 const SvdSec s = secs[si];
                 const BjSec b = bsecs[si];
-                if (bj_task(S, XW, XV, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax, inner_sweeps) &&
+                if (bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax, inner_sweeps) &&
                     threadIdx.x == 0)
                     atomicAdd(&rot[sweep], 1);
             }
@@ -404,26 +482,81 @@ int bjacobi_max_rows() { return (int)((BJ_SMEM_MAX - sizeof(BjShared)) / (BJ_LD 
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
                     int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c,
                     float* gmax, int* rot, int* sweeps, unsigned* bar, unsigned* err, cudaStream_t st) {
-    if (ntasks <= 0 || nrounds <= 0) return;
-    PD_REQUIRE(max_rows <= bjacobi_max_rows(), DMRG_ERR_CAPACITY, "block Jacobi: sector rows exceed shared memory");
-    max_rows = std::max(1, max_rows);
+    if (ntasks <= 0 || nrounds <= 0) {
+        PD_CK(cudaMemsetAsync(sweeps, 0, sizeof(int), st));
+        return;
+    }
+    // taller sectors are streamed through the staging area in chunks of max_rows rows
+    max_rows = std::max(1, std::min(max_rows, bjacobi_max_rows()));
     // W and V staged side by side when both fit (V then loads while W is processed)
     const size_t row_bytes = BJ_LD * sizeof(float);
     int split = sizeof(BjShared) + (size_t)(max_rows + max_n) * row_bytes <= (size_t)BJ_SMEM_MAX;
     const size_t smem = sizeof(BjShared) + (size_t)(split ? max_rows + max_n : max_rows) * row_bytes;
-    PD_CK(cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0, dev = 0, sms = 0;
-    PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, BJ_THREADS, smem));
-    PD_REQUIRE(per_sm > 0, DMRG_ERR_CAPACITY, "block Jacobi: kernel does not fit on an SM");
+    // the shared-memory ceiling is raised once per process to the largest size any launch uses
+    // (region threads launch concurrently with different sizes)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_bjacobi_round, cudaFuncAttributeMaxDynamicSharedMemorySize, BJ_SMEM_MAX);
+    PD_CK(attr);
+    int dev = 0, sms = 0;
     PD_CK(cudaGetDevice(&dev));
     PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = std::max(1, std::min(ntasks, per_sm * sms));
-    PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
-    void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&task_sec, (void*)&ntasks, (void*)&nrounds,
-                    (void*)&max_sweeps, (void*)&inner_sweeps, (void*)&max_rows, (void*)&split, (void*)&W, (void*)&V, (void*)&tol,
-                    (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps, (void*)&bar, (void*)&err};
-    PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi, blocks, BJ_THREADS, args, smem, st));
-    PD_LAUNCHED();
+    if (g_sm_cap == 0) {
+        // the GPU is this caller's: all sweeps in one cooperative launch
+        static const cudaError_t attr_c =
+            cudaFuncSetAttribute(k_bjacobi_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, BJ_SMEM_MAX);
+        PD_CK(attr_c);
+        int per_sm = 0;
+        PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi_coop, BJ_THREADS, smem));
+        PD_REQUIRE(per_sm > 0, DMRG_ERR_CAPACITY, "block Jacobi: kernel does not fit on an SM");
+        const int cblocks = std::max(1, std::min(ntasks, per_sm * sms));
+        PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+        void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&task_sec, (void*)&ntasks, (void*)&nrounds,
+                        (void*)&max_sweeps, (void*)&inner_sweeps, (void*)&max_rows, (void*)&split, (void*)&W,
+                        (void*)&V, (void*)&tol, (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps,
+                        (void*)&bar, (void*)&err};
+        PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi_coop, cblocks, BJ_THREADS, args, smem, st));
+        PD_LAUNCHED();
+        return;
+    }
+    // regions run concurrently: one launch per round, nothing spins
+    const int blocks = std::max(1, std::min(ntasks, 4 * sms));
+    // rounds are enqueued sweep by sweep; the host reads rot of sweep s - 1 after enqueuing sweep s
+    // (pinned copy + event), so the device never waits for the host; a sweep enqueued after the
+    // converged one returns at once.
+    int* hrot = sweep_flags_host(max_sweeps);
+    std::vector<cudaEvent_t> evs(max_sweeps, nullptr);
+    int done = max_sweeps;
+    try {
+        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+            for (int round = 0; round < nrounds; ++round) {
+                k_bjacobi_round<<<blocks, BJ_THREADS, smem, st>>>(secs, bsecs, task_sec, ntasks, round, sweep,
+                                                                   inner_sweeps, max_rows, split, W, V, tol, noise_c,
+                                                                   gmax, rot);
+                PD_LAUNCHED();
+            }
+            PD_CK(cudaMemcpyAsync(hrot + sweep, rot + sweep, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PD_CK(cudaEventCreateWithFlags(&evs[sweep], cudaEventDisableTiming));
+            PD_CK(cudaEventRecord(evs[sweep], st));
+            if (sweep > 0) {
+                PD_CK(cudaEventSynchronize(evs[sweep - 1]));
+                if (hrot[sweep - 1] == 0) {
+                    done = sweep;      // sweep - 1 rotated nothing; the launches of `sweep` exit at once
+                    break;
+                }
+            }
+        }
+        if (done == max_sweeps) {
+            PD_CK(cudaEventSynchronize(evs[max_sweeps - 1]));
+            if (hrot[max_sweeps - 1] == 0) done = max_sweeps;
+        }
+    } catch (...) {
+        for (auto e : evs)
+            if (e) cudaEventDestroy(e);
+        throw;
+    }
+    for (auto e : evs)
+        if (e) cudaEventDestroy(e);
+    PD_CK(cudaMemcpyAsync(sweeps, &done, sizeof(int), cudaMemcpyHostToDevice, st));
 }
 
 }  // namespace pd

@@ -212,9 +212,22 @@ void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_
     SplitResult r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
                               right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st, fp32);
     if (fp32) {
-        // the factor that joins a block must be orthonormal to FP64 accuracy
-        if (right) orthonormalize_factor(bl, r.mid, c->qn, A.as<double>(), true, st);
-        else orthonormalize_factor(r.mid, br, c->qn, B.as<double>(), false, st);
+        // the factor that joins a block must be orthonormal to FP64 accuracy; an FP32 split whose
+        // kept vectors are beyond the reach of the re-orthonormalisation (FP32 rounding left
+        // near-cutoff columns coupled) is redone in FP64
+        bool ok = true;
+        try {
+            if (right) orthonormalize_factor(bl, r.mid, c->qn, A.as<double>(), true, st);
+            else orthonormalize_factor(r.mid, br, c->qn, B.as<double>(), false, st);
+        } catch (const Error& e) {
+            if (e.st != DMRG_ERR_NUMERIC) throw;
+            ok = false;
+        }
+        if (!ok) {
+            prof_fallback();
+            r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
+                          right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st, false);
+        }
     }
     ch.bond[j + 1] = r.mid;
     ch.lam[j + 1] = r.lam;
@@ -323,12 +336,23 @@ void region_half_sweep(dmrg_ctx* c, Chain& r, bool right, const dmrg_sweep_param
 
 // Run fn(i) for i in items on one host thread each (every region drives its own stream).
 template <class F>
-void parallel_items(const std::vector<int>& items, F fn) {
+void parallel_items(const std::vector<int>& items, F fn, bool serial = false) {
+    if (serial || items.size() <= 1) {
+        // on the calling thread, one after another (each item has the GPU to itself)
+        for (int it : items) fn(it);
+        return;
+    }
     std::vector<std::thread> th;
     std::vector<Error> errs(items.size(), Error{DMRG_OK, ""});
+    int dev = 0, sms = 0;
+    PD_CK(cudaGetDevice(&dev));
+    PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int cap = items.size() > 1 ? std::max(1, sms / (int)items.size()) : 0;
     for (size_t t = 0; t < items.size(); ++t)
         th.emplace_back([&, t]() {
             try {
+                PD_CK(cudaSetDevice(dev));
+                g_sm_cap = cap;
                 fn(items[t]);
             } catch (const Error& e) {
                 errs[t] = e;
@@ -557,7 +581,7 @@ void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
     parallel_items(odd, [&](int k) {
         region_half_sweep(c, *c->reg[k], true, p);
         check_err_word(c->reg[k]->err.as<unsigned>(), c->reg[k]->st);
-    });
+    }, p->serial_regions != 0);
 }
 
 // One parallel sweep, Fig. 4 (a)-(d).
@@ -574,14 +598,14 @@ StepStats region_sweep(dmrg_ctx* c, const dmrg_sweep_params* p) {
             bool right = (k % 2 == 0) == first;
             region_half_sweep(c, *c->reg[k], right, p);
             check_err_word(c->reg[k]->err.as<unsigned>(), c->reg[k]->st);
-        });
+        }, p->serial_regions != 0);
     };
     std::vector<double> e_merge(R, 0.0);
     half(true);                                                         // (a)
-    parallel_items(mb, [&](int k) { do_merge(c, k, p, nullptr, &e_merge[k]); });   // (b)
+    parallel_items(mb, [&](int k) { do_merge(c, k, p, nullptr, &e_merge[k]); }, p->serial_regions != 0);   // (b)
     if (!mb.empty()) e_last = e_merge[mb.back()];
     half(false);                                                        // (c)
-    parallel_items(md, [&](int k) { do_merge(c, k, p, nullptr, &e_merge[k]); });   // (d)
+    parallel_items(md, [&](int k) { do_merge(c, k, p, nullptr, &e_merge[k]); }, p->serial_regions != 0);   // (d)
     if (!md.empty()) e_last = e_merge[md.back()];
     StepStats tot;
     for (auto& r : c->reg) tot.merge(r->acc);
@@ -608,6 +632,26 @@ StepStats region_sweep(dmrg_ctx* c, const dmrg_sweep_params* p) {
         return DMRG_ERR_STATE;                                \
     }
 
+namespace {
+// Work buffers come from the device's default stream-ordered pool.  With its default release
+// threshold (0) every stream synchronisation hands freed memory back to the driver, and the next
+// allocation maps it again; region threads that synchronise independently then spend their time
+// re-mapping.  Keep freed memory in the pool instead (process-wide, set once).
+void keep_pool_memory() {
+    static const cudaError_t st = [] {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        cudaMemPool_t pool;
+        e = cudaDeviceGetDefaultMemPool(&pool, dev);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        return cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }();
+    PD_CK(st);
+}
+}  // namespace
+
 extern "C" {
 
 dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_config* cfg) {
@@ -620,6 +664,7 @@ dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_c
     PD_REQUIRE(cfg->precision == DMRG_FP64 || cfg->precision == DMRG_TF32 || cfg->precision == DMRG_BF16,
                DMRG_ERR_ARG, "unknown precision");
     PD_REQUIRE(cfg->precision == DMRG_FP64 || tc_available(), DMRG_ERR_STATE, "tensor-core engine unavailable");
+    keep_pool_memory();
     std::unique_ptr<dmrg_ctx> C(new dmrg_ctx());
     c = C.get();
     C->L = mpo->n_sites;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <string>
@@ -49,8 +50,21 @@ bool prof_on();
 // prof_stop after); the elapsed time is resolved in dmrg_profile_read.
 void* prof_start(cudaStream_t st);
 void prof_stop(void* token, cudaStream_t st, int cls, double flops);
-// Jacobi SVD statistics (sweeps run per call), accumulated while profiling is on.
-void prof_svd(int sweeps, double ms);
+// Jacobi SVD statistics (sweeps run per call), accumulated while profiling is on; kind 0: FP32
+// scalar Jacobi, 1: FP32 block Jacobi, 2: FP64; max_rows: the call's largest sector row count.
+void prof_svd(int sweeps, double ms, int kind, int max_rows);
+// An FP32 split redone in FP64 (counted always, not only while profiling).
+void prof_fallback();
+
+// Persistent and cooperative grids are sized to the SMs of the device; while R regions run
+// concurrently (one host thread each), each thread caps its grids at sms / R so that the regions
+// share the GPU spatially instead of queueing behind each other's resident grids.
+extern thread_local int g_sm_cap;   // 0: no cap
+inline int sm_share(int sms) { return g_sm_cap > 0 ? std::max(1, std::min(sms, g_sm_cap)) : sms; }
+
+// Pinned host words (one per sweep, at least n) owned by the calling thread, for reading the
+// per-sweep rotation flags of the Jacobi kernels without a device-wide synchronisation.
+int* sweep_flags_host(int n);
 
 // Device error word bits (written by kernels, read by the host after a step).
 enum : unsigned {

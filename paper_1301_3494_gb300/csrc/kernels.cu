@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <vector>
 
 #include "grid_sync.cuh"
 #include "internal.h"
@@ -456,6 +457,22 @@ __global__ void k_jacobi_coop(const SvdSec* __restrict__ secs, const int* __rest
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = sweep + 1;
 }
 
+// One round of one sweep of the scalar Jacobi (one warp per pair); rot[sweep] set when a pair
+// rotated.  A launch whose previous sweep rotated nothing returns at once.
+template <class T>
+__global__ void k_jacobi_round(const SvdSec* __restrict__ secs, const int* __restrict__ pair_sec, int npairs,
+                               int round, int sweep, T* __restrict__ W, T* __restrict__ V, T tol,
+                               const double* __restrict__ floor2, int* __restrict__ rot) {
+    if (sweep > 0 && *((volatile int*)&rot[sweep - 1]) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= npairs) return;
+    const int si = pair_sec[w];
+    const SvdSec s = secs[si];
+    if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, floor2 ? (T)floor2[si] : T(0), lane) && lane == 0)
+        rot[sweep] = 1;
+}
+
 // floor2[s] = (eta * |W_s|_F)^2: columns below it are left unrotated (below working precision).
 template <class T>
 __global__ void k_svd_floor(const SvdSec* __restrict__ secs, const T* __restrict__ W, double eta,
@@ -714,6 +731,43 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
         fl = floor2;
     }
     const int threads = 128;   // register-heavy pair updates: small blocks keep several per SM
+    if (g_sm_cap > 0) {
+        // regions run concurrently: one launch per round (no grid barrier spinning on SMs that
+        // other regions' kernels need), convergence read one sweep behind
+        const int grid = (npairs * 32 + threads - 1) / threads;
+        int* hrot = sweep_flags_host(max_sweeps);
+        std::vector<cudaEvent_t> evs(max_sweeps, nullptr);
+        int done = max_sweeps;
+        auto cleanup = [&]() {
+            for (auto e : evs)
+                if (e) cudaEventDestroy(e);
+        };
+        try {
+            for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+                for (int round = 0; round < maxnpad - 1; ++round) {
+                    k_jacobi_round<T><<<grid, threads, 0, st>>>(secs, pair_sec, npairs, round, sweep, W, V, tol, fl,
+                                                                rot);
+                    PD_LAUNCHED();
+                }
+                PD_CK(cudaMemcpyAsync(hrot + sweep, rot + sweep, sizeof(int), cudaMemcpyDeviceToHost, st));
+                PD_CK(cudaEventCreateWithFlags(&evs[sweep], cudaEventDisableTiming));
+                PD_CK(cudaEventRecord(evs[sweep], st));
+                if (sweep > 0) {
+                    PD_CK(cudaEventSynchronize(evs[sweep - 1]));
+                    if (hrot[sweep - 1] == 0) {
+                        done = sweep;
+                        break;
+                    }
+                }
+            }
+        } catch (...) {
+            cleanup();
+            throw;
+        }
+        cleanup();
+        PD_CK(cudaMemcpyAsync(sweeps, &done, sizeof(int), cudaMemcpyHostToDevice, st));
+        return;
+    }
     static int per_sm[2] = {0, 0};
     int& ps = per_sm[sizeof(T) == 8 ? 1 : 0];
     if (!ps) PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_jacobi_coop<T>, threads, 0));
@@ -721,7 +775,7 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
     PD_CK(cudaGetDevice(&dev));
     PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int need = (npairs * 32 + threads - 1) / threads;
-    int blocks = std::max(1, std::min(need, ps * sms));
+    int blocks = std::max(1, std::min(need, ps * sm_share(sms)));
     PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
     void* args[] = {(void*)&secs, (void*)&pair_sec, (void*)&npairs, (void*)&maxnpad, (void*)&max_sweeps,
                     (void*)&W, (void*)&V, (void*)&tol, (void*)&fl, (void*)&rot, (void*)&sweeps, (void*)&bar,

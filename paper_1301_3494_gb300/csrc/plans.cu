@@ -378,7 +378,8 @@ void orthonormalize_factor(const Sec& bl, const Sec& br, const std::vector<int>&
         double worst = 0.0;
         for (double v : hdev) worst = std::max(worst, v);
         PD_REQUIRE(std::isfinite(worst) && worst < 0.9, DMRG_ERR_NUMERIC,
-                   "kept singular vectors too far from orthonormal for the FP64 re-orthonormalisation");
+                   "kept singular vectors too far from orthonormal for the FP64 re-orthonormalisation (|I - X^T X| = " +
+                       std::to_string(worst) + " at iteration " + std::to_string(iter) + ")");
         if (worst < 1e-13 || iter == 5) break;
         // X <- X (3I - G)/2 (left) or (3I - G)/2 X (right): one Newton-Schulz step
         k_ns_prep<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<NsJob>(), G.as<double>(),
@@ -1322,7 +1323,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it; the
         // kept factor that joins a block is re-orthonormalised in FP64 afterwards
         const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)maxp));
-        if (maxp <= bjacobi_max_rows()) {
+        {
             // block Jacobi: one task per block pair, n / 16 - 1 rounds per sweep
             std::vector<BjSec> bs(nsec);
             std::vector<int> task_sec;
@@ -1345,10 +1346,6 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
             launch_bjacobi(dsecs.as<SvdSec>(), dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, maxp, maxn, 40,
                            2, dW.as<float>(), dV.as<float>(), tol, 8.0f * FLT_EPSILON, dgmax.as<float>(),
                            drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr, st);
-        } else {
-            launch_jacobi<float>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, 40, dW.as<float>(),
-                                 dV.as<float>(), tol, 0.0, dfloor.as<double>(), drot.as<int>(),
-                                 drot.as<int>() + max_sweeps, bar, jerr, st);
         }
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
@@ -1375,7 +1372,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         PD_CK(cudaStreamSynchronize(st));
         float ms = 0.f;
         PD_CK(cudaEventElapsedTime(&ms, sv0, sv1));
-        prof_svd(sweeps, ms);
+        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp);
         cudaEventDestroy(sv0);
         cudaEventDestroy(sv1);
     }
@@ -1390,12 +1387,16 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     std::vector<int> kept(nsec);
     double wts[2];
     unsigned jerr_h = 0;
+    int sweeps_h = 0;
+    PD_CK(cudaMemcpyAsync(&sweeps_h, drot.as<int>() + max_sweeps, 4, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(&jerr_h, jerr, 4, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(kept.data(), dkept.p, 4 * nsec, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(wts, dwts.p, 16, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
     PD_REQUIRE(!(jerr_h & ERRBIT_TIMEOUT), DMRG_ERR_TIMEOUT, "Jacobi SVD grid barrier timed out");
     SplitResult res;
+    res.sweeps = sweeps_h;
+    res.max_rows = maxp;
     std::vector<int> kept_of_sec(nsec, 0);
     for (int s = 0; s < nsec; ++s)
         if (kept[s] > 0) {

@@ -305,6 +305,8 @@ struct SplitResult {
     Sec mid;                      // kept sectors of the new middle bond
     std::vector<double> lam;      // kept lambda (normalised), sector order, descending inside
     double trunc = 0.0;
+    int sweeps = 0;               // Jacobi sweeps run
+    int max_rows = 0;             // largest sector row count
 };
 // lam_pow_left/right: 0 or 1 -> A (left factor) multiplied by Lambda^pow_left, B by Lambda^pow_right.
 SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,

@@ -1,4 +1,5 @@
 // Process-wide instrumentation: kernel-launch counter and event timing of grouped GEMMs.
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -6,7 +7,32 @@
 
 namespace pd {
 
+thread_local int g_sm_cap = 0;
+
+namespace {
+struct PinnedWords {
+    int* p = nullptr;
+    int n = 0;
+    ~PinnedWords() {
+        if (p) cudaFreeHost(p);
+    }
+};
+thread_local PinnedWords g_flags;
+}  // namespace
+
+int* sweep_flags_host(int n) {
+    if (g_flags.n < n) {
+        if (g_flags.p) PD_CK(cudaFreeHost(g_flags.p));
+        g_flags.p = nullptr;
+        g_flags.n = 0;
+        PD_CK(cudaMallocHost(&g_flags.p, sizeof(int) * (size_t)n));
+        g_flags.n = n;
+    }
+    return g_flags.p;
+}
+
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_fallbacks{0};
 thread_local int g_prof_class = PROF_MV;
 
 namespace {
@@ -18,13 +44,15 @@ struct Rec {
 std::mutex g_mu;
 std::atomic<bool> g_on{false};
 std::vector<Rec> g_pending;
-long long g_svd_calls = 0, g_svd_sweeps = 0;
-double g_svd_ms = 0.0;
+long long g_svd_calls = 0, g_svd_sweeps = 0, g_svd_block = 0, g_svd_f64 = 0, g_svd_rows = 0;
+double g_svd_ms = 0.0, g_svd_block_ms = 0.0, g_svd_f64_ms = 0.0;
 double g_ms[4] = {0, 0, 0, 0}, g_fl[4] = {0, 0, 0, 0};
 long long g_n[4] = {0, 0, 0, 0};
 }  // namespace
 
 bool prof_on() { return g_on.load(std::memory_order_relaxed); }
+
+void prof_fallback() { g_fallbacks.fetch_add(1); }
 
 void* prof_start(cudaStream_t st) {
     cudaEvent_t* ev = new cudaEvent_t[2];
@@ -42,11 +70,14 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops) {
     delete[] ev;
 }
 
-void prof_svd(int sweeps, double ms) {
+void prof_svd(int sweeps, double ms, int kind, int max_rows) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_svd_calls += 1;
     g_svd_sweeps += sweeps;
     g_svd_ms += ms;
+    if (kind == 1) g_svd_block += 1, g_svd_block_ms += ms;
+    if (kind == 2) g_svd_f64 += 1, g_svd_f64_ms += ms;
+    g_svd_rows = std::max<long long>(g_svd_rows, max_rows);
 }
 
 }  // namespace pd
@@ -66,9 +97,10 @@ void dmrg_profile_reset(void) {
     }
     g_pending.clear();
     for (int i = 0; i < 4; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
-    g_svd_calls = g_svd_sweeps = 0;
-    g_svd_ms = 0.0;
+    g_svd_calls = g_svd_sweeps = g_svd_block = g_svd_f64 = g_svd_rows = 0;
+    g_svd_ms = g_svd_block_ms = g_svd_f64_ms = 0.0;
     g_launches.store(0);
+    g_fallbacks.store(0);
 }
 
 dmrg_status dmrg_profile_read(dmrg_profile* out) {
@@ -102,6 +134,12 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->svd_calls = g_svd_calls;
     out->svd_sweeps = g_svd_sweeps;
     out->svd_ms = g_svd_ms;
+    out->svd_block_calls = g_svd_block;
+    out->svd_fp64_calls = g_svd_f64;
+    out->svd_block_ms = g_svd_block_ms;
+    out->svd_fp64_ms = g_svd_f64_ms;
+    out->svd_max_rows = g_svd_rows;
+    out->svd_fp64_fallbacks = g_fallbacks.load();
     return DMRG_OK;
 }
 

@@ -373,12 +373,9 @@ void launch_tc(GemmBatch& g, const CUtensorMap& ma, const CUtensorMap& mb, int l
     constexpr int STAGE_BYTES = BM * 128 + BN * 128;
     constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
     auto kern = k_tc_gemm<KIND, BN, STAGES, OutT>;
-    static bool attr = false;
-    if (!attr) {
-        PD_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-        attr = true;
-    }
-    int grid = std::min(g.ntiles, sm_count());
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    PD_CK(attr);
+    int grid = std::min(g.ntiles, sm_share(sm_count()));
     void* tok = prof_on() ? prof_start(st) : nullptr;
     kern<<<grid, THREADS, SMEM, st>>>(ma, mb, g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles,
                                       lda, ldb, (OutT*)C, err);

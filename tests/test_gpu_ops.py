@@ -164,7 +164,8 @@ def test_svd_split_accurate_graded(kind, m, seed):
         assert np.abs(rec_g[k] - rec_o[k]).max() <= 1e-12 * lam_ref.max(), k
 
 
-@pytest.mark.parametrize("kind,m,mmax", [("chain", 200, 120), ("cyl", 160, 90), ("cyl", 420, 300), ("tfim", 80, 50)])
+@pytest.mark.parametrize("kind,m,mmax", [("chain", 200, 120), ("cyl", 160, 90), ("cyl", 420, 300), ("tfim", 80, 50),
+                                          ("chain", 3200, 2000)])
 def test_svd_split_fp32_block_jacobi(kind, m, mmax):
     """Mixed-precision split (FP32 block Jacobi, A re-orthonormalised in FP64) against the FP64
     oracle.  FP32 columns carry absolute errors ~eps_f32 * lambda_max and pairs stop rotating at a
