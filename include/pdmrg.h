@@ -224,6 +224,7 @@ typedef struct {
     double svd_fp64_ms;          /* device time of the FP64 splits                              */
     long long svd_max_rows;      /* largest sector row count seen                               */
     long long svd_fp64_fallbacks; /* FP32 splits redone in FP64 (re-orthonormalisation refused)  */
+    double svd_block_flops;      /* FP32 Gram + column-rotation flops of the block-Jacobi splits */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);

@@ -42,7 +42,7 @@ class Profile(C.Structure):
                 ("f32_gemm_flops", C.c_double), ("svd_calls", C.c_longlong), ("svd_sweeps", C.c_longlong),
                 ("svd_ms", C.c_double), ("svd_block_calls", C.c_longlong), ("svd_fp64_calls", C.c_longlong),
                 ("svd_block_ms", C.c_double), ("svd_fp64_ms", C.c_double), ("svd_max_rows", C.c_longlong),
-                ("svd_fp64_fallbacks", C.c_longlong)]
+                ("svd_fp64_fallbacks", C.c_longlong), ("svd_block_flops", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

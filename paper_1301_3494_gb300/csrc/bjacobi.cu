@@ -288,27 +288,30 @@ __device__ __forceinline__ void bj_rotate_streamed(float* __restrict__ X, float*
     }
 }
 
-// One block pair.  Returns true (in every thread) if it rotated.  XW holds `cap` staged rows; XV
+// One block pair.  Returns (in every thread) the FP32 flops of its Gram matrix and, if it rotated,
+// of the column rotations (negative when it rotated: -flops), 0 when the round has no task for
+// it.  XW holds `cap` staged rows; XV
 // (n rows) is a separate area when `split` (V then loads while W is processed), else it aliases
 // XW.  A sector taller than cap is streamed through XW in row chunks (its W is read twice: once
 // for the Gram matrix, once for the rotation).
-__device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__ XV, int cap, const SvdSec& s,
+__device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__ XV, int cap, const SvdSec& s,
                         const BjSec& b, int si, int pi, int round, float* __restrict__ W, float* __restrict__ V,
                         float tol, float noise_c, float* __restrict__ gmax, int inner_sweeps) {
     int cI, kI, cJ, kJ;
     if (b.nb == 1) {
-        if (round != 0) return false;
+        if (round != 0) return 0.0;
         cI = 0; kI = s.n; cJ = 0; kJ = 0;
     } else {
-        if (round >= b.nbp - 1) return false;
+        if (round >= b.nbp - 1) return 0.0;
         int I = rr_pos(pi, round, b.nbp), J = rr_pos(b.nbp - 1 - pi, round, b.nbp);
         if (I > J) { const int t = I; I = J; J = t; }
-        if (J >= b.nb) return false;
+        if (J >= b.nb) return 0.0;
         cI = I * BJ_B; kI = min(BJ_B, s.n - cI);
         cJ = J * BJ_B; kJ = min(BJ_B, s.n - cJ);
     }
     const int k = kI + kJ;
     const int tid = threadIdx.x;
+    const double gram_flops = 2.0 * s.p * k * k, rot_flops = 2.0 * ((double)s.p + s.n) * k * k;
     const bool resident = s.p <= cap;                 // W's columns fit: staged once
     const bool split = resident && XV != XW;          // and V's alongside
     if (tid < BJ_K) S.gcol[tid] = tid < kI ? cI + tid : (tid < k ? cJ + tid - kI : -1);
@@ -363,7 +366,7 @@ __device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__
     if (!__syncthreads_or(need)) {
         cp_async_wait<0>();
         __syncthreads();
-        return false;
+        return gram_flops;
     }
     bj_inner(S, inner_sweeps, tol, noise);
     // order the eigenvectors by decreasing eigenvalue (ties: lower index first)
@@ -393,14 +396,14 @@ __device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__
             __syncthreads();
             bj_unstage(XV, V + s.v_off, s.n, 0, s.n, S.gcol, k);
             __syncthreads();
-            return true;
+            return -(gram_flops + rot_flops);
         }
         __syncthreads();
     } else {
         bj_rotate_streamed(XW, W + s.w_off, s.p, s.p, cap, Qp, S.gcol, k);
     }
     bj_rotate_streamed(XW, V + s.v_off, s.n, s.n, cap, Qp, S.gcol, k);
-    return true;
+    return -(gram_flops + rot_flops);
 }
 
 // One round of one sweep: every CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -410,7 +413,8 @@ __device__ bool bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__
 __global__ void __launch_bounds__(BJ_THREADS, 1)
     k_bjacobi_round(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
                     int ntasks, int round, int sweep, int inner_sweeps, int max_p, int split, float* __restrict__ W,
-                    float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax, int* __restrict__ rot) {
+                    float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax, int* __restrict__ rot,
+                    unsigned long long* __restrict__ flops) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     if (sweep > 0 && *((volatile int*)&rot[sweep - 1]) == 0) return;
     BjShared& S = *reinterpret_cast<BjShared*>(bj_smem);
@@ -423,14 +427,17 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
         S.hi[rnd][i] = (unsigned char)max(a, b);
     }
     __syncthreads();
+    double fl = 0.0;
     for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
         const int si = task_sec[t];
         const SvdSec s = secs[si];
         const BjSec b = bsecs[si];
-        if (bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax, inner_sweeps) &&
-            threadIdx.x == 0)
-            atomicAdd(&rot[sweep], 1);
+        const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax,
+                                 inner_sweeps);
+        fl += fabs(r);
+        if (r < 0.0 && threadIdx.x == 0) atomicAdd(&rot[sweep], 1);
     }
+    if (threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, (unsigned long long)fl);
 }
 
 // All sweeps in one cooperative launch, for a caller that has the GPU to itself: a bounded grid
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
                    int ntasks, int nrounds, int max_sweeps, int inner_sweeps, int max_p, int split,
                    float* __restrict__ W, float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax,
                    int* __restrict__ rot, int* __restrict__ sweeps, unsigned* __restrict__ bar,
-                   unsigned* __restrict__ err) {
+                   unsigned* __restrict__ err, unsigned long long* __restrict__ flops) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     BjShared& S = *reinterpret_cast<BjShared*>(bj_smem);
     float* XW = reinterpret_cast<float*>(bj_smem + sizeof(BjShared));
@@ -455,6 +462,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
     __syncthreads();
     int done = 0;
     bool alive = true;
+    double fl = 0.0;
     while (done < max_sweeps && alive) {
         const int sweep = done;
         for (int round = 0; round < nrounds && alive; ++round) {
@@ -462,9 +470,10 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
                 const int si = task_sec[t];
                 const SvdSec s = secs[si];
                 const BjSec b = bsecs[si];
-                if (bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax, inner_sweeps) &&
-                    threadIdx.x == 0)
-                    atomicAdd(&rot[sweep], 1);
+                const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax,
+                                         inner_sweeps);
+                fl += fabs(r);
+                if (r < 0.0 && threadIdx.x == 0) atomicAdd(&rot[sweep], 1);
             }
             alive = grid_barrier(bar, gridDim.x, err);
         }
@@ -472,6 +481,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
         ++done;
         if (*((volatile int*)&rot[sweep]) == 0) break;
     }
+    if (threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, (unsigned long long)fl);
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = done;
 }
 
@@ -481,7 +491,8 @@ int bjacobi_max_rows() { return (int)((BJ_SMEM_MAX - sizeof(BjShared)) / (BJ_LD 
 
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
                     int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c,
-                    float* gmax, int* rot, int* sweeps, unsigned* bar, unsigned* err, cudaStream_t st) {
+                    float* gmax, int* rot, int* sweeps, unsigned* bar, unsigned* err, unsigned long long* flops,
+                    cudaStream_t st) {
     if (ntasks <= 0 || nrounds <= 0) {
         PD_CK(cudaMemsetAsync(sweeps, 0, sizeof(int), st));
         return;
@@ -513,7 +524,7 @@ void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec,
         void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&task_sec, (void*)&ntasks, (void*)&nrounds,
                         (void*)&max_sweeps, (void*)&inner_sweeps, (void*)&max_rows, (void*)&split, (void*)&W,
                         (void*)&V, (void*)&tol, (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps,
-                        (void*)&bar, (void*)&err};
+                        (void*)&bar, (void*)&err, (void*)&flops};
         PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi_coop, cblocks, BJ_THREADS, args, smem, st));
         PD_LAUNCHED();
         return;
@@ -531,7 +542,7 @@ void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec,
             for (int round = 0; round < nrounds; ++round) {
                 k_bjacobi_round<<<blocks, BJ_THREADS, smem, st>>>(secs, bsecs, task_sec, ntasks, round, sweep,
                                                                    inner_sweeps, max_rows, split, W, V, tol, noise_c,
-                                                                   gmax, rot);
+                                                                   gmax, rot, flops);
                 PD_LAUNCHED();
             }
             PD_CK(cudaMemcpyAsync(hrot + sweep, rot + sweep, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -51,8 +51,9 @@ bool prof_on();
 void* prof_start(cudaStream_t st);
 void prof_stop(void* token, cudaStream_t st, int cls, double flops);
 // Jacobi SVD statistics (sweeps run per call), accumulated while profiling is on; kind 0: FP32
-// scalar Jacobi, 1: FP32 block Jacobi, 2: FP64; max_rows: the call's largest sector row count.
-void prof_svd(int sweeps, double ms, int kind, int max_rows);
+// scalar Jacobi, 1: FP32 block Jacobi, 2: FP64; max_rows: the call's largest sector row count;
+// flops: the FP32 Gram and rotation flops of a block-Jacobi call.
+void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops);
 // An FP32 split redone in FP64 (counted always, not only while profiling).
 void prof_fallback();
 
@@ -209,7 +210,7 @@ struct BjSec {
 int bjacobi_max_rows();
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
                     int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c, float* gmax,
-                    int* rot, int* sweeps, unsigned* bar, unsigned* err, cudaStream_t st);
+                    int* rot, int* sweeps, unsigned* bar, unsigned* err, unsigned long long* flops, cudaStream_t st);
 template <class T>
 void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st);
 

@@ -1291,7 +1291,8 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         }
         gather.add(j);
     }
-    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dfloor, dbar;
+    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dfloor, dbar, dflops;
+    dflops.ensure(8, st);
     const int max_sweeps = 60;
     dfloor.ensure(std::max(1, nsec) * 8, st);
     dbar.ensure(4 * sizeof(unsigned), st);     // barrier words + the error word
@@ -1343,9 +1344,11 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
             upload(dts, task_sec, st);
             dgmax.ensure(std::max(1, nsec) * 4, st);
             PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
+            PD_CK(cudaMemsetAsync(dflops.p, 0, 8, st));
             launch_bjacobi(dsecs.as<SvdSec>(), dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, maxp, maxn, 40,
                            2, dW.as<float>(), dV.as<float>(), tol, 8.0f * FLT_EPSILON, dgmax.as<float>(),
-                           drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr, st);
+                           drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr,
+                           dflops.as<unsigned long long>(), st);
         }
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
@@ -1368,11 +1371,13 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     if (sv0) {
         PD_CK(cudaEventRecord(sv1, st));
         int sweeps = 0;
+        unsigned long long fl = 0;
         PD_CK(cudaMemcpyAsync(&sweeps, drot.as<int>() + max_sweeps, 4, cudaMemcpyDeviceToHost, st));
+        if (fp32) PD_CK(cudaMemcpyAsync(&fl, dflops.p, 8, cudaMemcpyDeviceToHost, st));
         PD_CK(cudaStreamSynchronize(st));
         float ms = 0.f;
         PD_CK(cudaEventElapsedTime(&ms, sv0, sv1));
-        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp);
+        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl);
         cudaEventDestroy(sv0);
         cudaEventDestroy(sv1);
     }
