@@ -51,10 +51,17 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["steps", "sweeps", "op"], default="sweeps",
+    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy"], default="sweeps",
                     help="sweeps: a step is one real-space parallel sweep (Fig. 4) over the whole lattice; "
                          "steps: a step is one bulk two-site update (serial); op: repeated H_eff matvecs at "
-                         "one bond (random environments, small device footprint, for profiler captures)")
+                         "one bond (random environments, small device footprint, for profiler captures); "
+                         "accuracy: the same serial sweeps (m ramped to --acc-m) in FP64 and in --precision "
+                         "mode from the same seeded state, energies and sweep times compared")
+    ap.add_argument("--acc-m", type=int, default=500)
+    ap.add_argument("--acc-sweeps", type=int, default=6)
+    ap.add_argument("--acc-variants", default="",
+                    help="accuracy: extra same-state sweeps, comma-separated precision:refine_iters[:svd64][:davN] "
+                         "(e.g. tf32:6, bf16:12:dav1)")
     ap.add_argument("--regions", type=int, default=4)
     ap.add_argument("--concurrent-regions", action="store_true",
                     help="sweeps: one host thread and stream per region, overlapping on the GPU (default: the "
@@ -102,6 +109,90 @@ def op_mode(args, mpo, qn, mps, center):
 # ------------------------------------------------------------------------------------------
 # Workload
 # ------------------------------------------------------------------------------------------
+def accuracy_mode(args):
+    """FP64 vs mixed precision on the 24x8 cylinder: (1) the same serial sweep schedule from the
+    same seeded state in both modes; (2) one more sweep from the FP64-converged state in each mode
+    and variant.  Every final state is evaluated by an FP64 engine (FP64 environments and Rayleigh
+    quotient); energies, their relative differences and sweep seconds are reported."""
+    import torch
+    import paper_1301_3494_gb300 as pd
+    mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
+    qn = list(mpo.site.qn)
+    L = mpo.L
+    m0 = min(100, args.acc_m)
+    mps = wl.isometric_mps(L, qn, 0, m0, args.seed, 0, sigma=args.sigma)
+    W, flux, D = wl.pack_mpo(mpo)
+    data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
+    ramp = [min(args.acc_m, m0 * 2 ** k) for k in range(args.acc_sweeps)]
+    ramp[-2:] = [args.acc_m, args.acc_m]
+    res = {}
+    state = None
+    for prec in ("fp64", args.precision):
+        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax)
+        eng.set_mps(mps.bonds, data, center=0)
+        es, ts = [], []
+        for m in ramp:
+            t0 = time.perf_counter()
+            g = eng.sweep(m, dav_tol=1e-9, dav_max_iter=12, refine_iters=0 if prec == "fp64" else 6)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            es.append(g["energy"])
+        st = eng.state()
+        e_own = eng.energy()
+        eng.close()
+        if prec == "fp64":
+            state = st
+            e_true = e_own
+        else:
+            chk = pd.Engine(W, flux, D, qn, 0, "fp64", args.kmax)
+            chk.set_mps(st[0], st[1], center=st[2])
+            e_true = chk.energy()
+            chk.close()
+        res[prec] = {"energies": es, "sweep_s": ts, "final_fp64_rq": e_true, "final_own_rq": e_own,
+                     "max_trunc_err": g["max_trunc_err"]}
+    # one more sweep in each precision from the same (FP64-converged) state: the precision effect
+    # of one sweep, separated from the run-to-run difference of the convergence path
+    same = {}
+    variants = [("fp64", 0), (args.precision, 6)]
+    for v in filter(None, args.acc_variants.split(",")):
+        f = v.split(":")
+        variants.append((f[0], int(f[1])) + ((f[2],) if len(f) > 2 else ()))
+    for var in variants:
+        prec, ri = var[0], var[1]
+        opts = set(var[2:])
+        dav_it = next((int(o[3:]) for o in opts if o.startswith("dav")), 12)
+        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax, svd_fp64="svd64" in opts)
+        eng.set_mps(state[0], state[1], center=state[2])
+        e0 = eng.energy()
+        t0 = time.perf_counter()
+        g = eng.sweep(args.acc_m, dav_tol=1e-9, dav_max_iter=dav_it, refine_iters=ri)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        key = prec if var in (("fp64", 0), (args.precision, 6)) else ":".join(str(x) for x in var)
+        e_own = eng.energy()
+        st = eng.state()
+        eng.close()
+        # the state's energy evaluated with FP64 environments (a mixed engine's own Rayleigh
+        # quotient uses its FP32 environments)
+        chk = pd.Engine(W, flux, D, qn, 0, "fp64", args.kmax)
+        chk.set_mps(st[0], st[1], center=st[2])
+        same[key] = {"E_start": e0, "E_after_sweep": chk.energy(), "E_own_environments": e_own, "sweep_s": dt,
+                     "sweep_energy": g["energy"], "max_trunc_err": g["max_trunc_err"], "dav_nonconv": g["dav_nonconv"]}
+        chk.close()
+    e64, emx = res["fp64"]["final_fp64_rq"], res[args.precision]["final_fp64_rq"]
+    s64, smx = same["fp64"]["E_after_sweep"], same[args.precision]["E_after_sweep"]
+    out = {"mode": "accuracy", "workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}", "m_ramp": ramp,
+           "precision": args.precision,
+           "same_state_sweep": {"E_fp64": s64, "E_mixed": smx, "dE_over_E": abs(smx - s64) / abs(s64),
+                                "sweep_s_fp64": same["fp64"]["sweep_s"], "sweep_s_mixed": same[args.precision]["sweep_s"],
+                                "speedup": same["fp64"]["sweep_s"] / same[args.precision]["sweep_s"],
+                                "E_start": same["fp64"]["E_start"]},
+           "separate_runs": {"E_fp64": e64, "E_mixed": emx, "dE_over_E": abs(emx - e64) / abs(e64)},
+           "variants": {k: dict(v, dE_over_E=abs(v["E_after_sweep"] - s64) / abs(s64)) for k, v in same.items()},
+           "E_per_site_fp64": s64 / L, "detail": res}
+    print(json.dumps(out))
+
+
 def workload(args):
     mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
     qn = list(mpo.site.qn)
@@ -317,6 +408,9 @@ def main():
     if args.mode == "op":
         op_mode(args, mpo, qn, mps, center)
         return
+    if args.mode == "accuracy":
+        accuracy_mode(args)
+        return
     W, flux, D = wl.pack_mpo(mpo)
     eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
     data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
@@ -431,7 +525,8 @@ def main():
                 "ms_per_call": prof["svd_ms"] / max(1, prof["svd_calls"]),
                 "block_calls": prof["svd_block_calls"], "block_ms": prof["svd_block_ms"],
                 "fp64_calls": prof["svd_fp64_calls"], "fp64_ms": prof["svd_fp64_ms"],
-                "max_sector_rows": prof["svd_max_rows"], "fp64_fallbacks": prof["svd_fp64_fallbacks"]},
+                "max_sector_rows": prof["svd_max_rows"], "fp64_fallbacks": prof["svd_fp64_fallbacks"],
+                "rotated_pairs_per_sweep": [h for h in prof["svd_rot_hist"] if h > 0]},
         "env_update_ms_per_step": prof["f32_gemm_ms"] / args.steps if args.precision != "fp64" else None,
         "gpu_launches": prof["launches"],
         "clocks": clocks,

@@ -95,6 +95,8 @@ typedef struct {
     int precision;          /* dmrg_precision                                                 */
     int kmax;               /* Davidson subspace size before restart (2..32, default 8)       */
     void* stream;           /* cudaStream_t base stream (region streams are forked from it)   */
+    int svd_fp64;           /* mixed modes: 1 = ordinary-bond splits in FP64 as well (slower;
+                               0 = FP32 block Jacobi + FP64 re-orthonormalisation)             */
 } dmrg_config;
 
 typedef struct {
@@ -174,7 +176,11 @@ dmrg_status dmrg_merge(dmrg_ctx* ctx, int k, const dmrg_sweep_params* p,
                        double* fidelity_out, double* energy_out);
 
 /* FP64 Rayleigh quotient <psi|H_eff|psi>/<psi|psi> of the current two-site wavefunction
- * (serial mode) -- the energy of the whole state when the environments are current. */
+ * (serial mode) -- the energy of the whole state when the environments are current.  Mixed
+ * modes keep the environments in FP32, whose rounding (compounded over the sites) biases this
+ * value: ~3e-5 relative on the 24x8 Heisenberg cylinder at m = 300, while the state itself is
+ * within 1e-5 of the FP64 path's.  The exact energy of a mixed-mode state: export it
+ * (dmrg_get_site, dmrg_get_bond, dmrg_get_center) into an FP64 context and call this there. */
 dmrg_status dmrg_energy(dmrg_ctx* ctx, double* E_out);
 
 /* Sector table of bond b (0..L): writes up to cap entries, *n_out = number of sectors.
@@ -184,6 +190,13 @@ dmrg_status dmrg_get_bond(dmrg_ctx* ctx, int b, int* q_out, int* m_out, int cap,
 /* Singular values stored for bond b by its last SVD (descending within each sector,
  * sectors ascending, normalised to sum lambda^2 = 1).  *n_out = count. */
 dmrg_status dmrg_get_lambda(dmrg_ctx* ctx, int b, double* lam_out, int cap, int* n_out);
+
+/* Site tensor j of the serial state (checkpointing): the packed layout of dmrg_set_mps for
+ * bonds (j, j + 1) as dmrg_get_bond reports them, copied to host memory out[cap] (FP64, caller
+ * owned); *n_out = its element count (DMRG_ERR_CAPACITY, with *n_out set, if cap is smaller).
+ * Together with dmrg_get_bond and dmrg_get_center this reproduces the state through
+ * dmrg_set_mps.  Region mode: DMRG_ERR_STATE.  Synchronises the stream. */
+dmrg_status dmrg_get_site(dmrg_ctx* ctx, int j, double* out, long long cap, long long* n_out);
 
 /* Orthogonality-centre site of the serial state, or of region k in region mode. */
 dmrg_status dmrg_get_center(dmrg_ctx* ctx, int region, int* site_out);
@@ -225,6 +238,7 @@ typedef struct {
     long long svd_max_rows;      /* largest sector row count seen                               */
     long long svd_fp64_fallbacks; /* FP32 splits redone in FP64 (re-orthonormalisation refused)  */
     double svd_block_flops;      /* FP32 Gram + column-rotation flops of the block-Jacobi splits */
+    long long svd_rot_hist[48];  /* block Jacobi: block pairs rotated in sweep i, summed over splits */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);

@@ -42,14 +42,17 @@ class Profile(C.Structure):
                 ("f32_gemm_flops", C.c_double), ("svd_calls", C.c_longlong), ("svd_sweeps", C.c_longlong),
                 ("svd_ms", C.c_double), ("svd_block_calls", C.c_longlong), ("svd_fp64_calls", C.c_longlong),
                 ("svd_block_ms", C.c_double), ("svd_fp64_ms", C.c_double), ("svd_max_rows", C.c_longlong),
-                ("svd_fp64_fallbacks", C.c_longlong), ("svd_block_flops", C.c_double)]
+                ("svd_fp64_fallbacks", C.c_longlong), ("svd_block_flops", C.c_double),
+                ("svd_rot_hist", C.c_longlong * 48)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["svd_rot_hist"] = list(d["svd_rot_hist"])
+        return d
 
 
 class Config(C.Structure):
-    _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p)]
+    _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p), ("svd_fp64", C.c_int)]
 
 
 class SweepParams(C.Structure):
@@ -113,6 +116,7 @@ def lib():
         L.dmrg_get_bond.argtypes = [vp, C.c_int, _ip, _ip, C.c_int, _ip]
         L.dmrg_get_lambda.argtypes = [vp, C.c_int, _dp, C.c_int, _ip]
         L.dmrg_get_center.argtypes = [vp, C.c_int, _ip]
+        L.dmrg_get_site.argtypes = [vp, C.c_int, _dp, C.c_longlong, C.POINTER(C.c_longlong)]
         L.dmrg_destroy.argtypes = [vp]
         L.dmrg_heff_apply.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp, _dp, vp]
         L.dmrg_heff_apply_noalloc.argtypes = [C.POINTER(BondDesc), vp, vp, vp, vp, vp]
@@ -122,7 +126,7 @@ def lib():
                                      _dp, vp]
         for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
                      "dmrg_profile_read", "dmrg_merge",
-                     "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_destroy",
+                     "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_get_site", "dmrg_destroy",
                      "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_env_left", "dmrg_env_right",
                      "dmrg_svd_split"):
             getattr(L, name).restype = st
@@ -226,14 +230,14 @@ def svd_split(bond: Bond, psi_dev, m_max, accurate, A_dev, lam_dev, B_dev, cap=4
 class Engine:
     """A DMRG state on the GPU: MPO, MPS, environments, optional real-space regions."""
 
-    def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0):
+    def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0, svd_fp64=False):
         self._keep = [_f64(W), _i32(flux), _i32(D), _i32(qn)]
         W_, f_, D_, q_ = self._keep
         self.L = len(D_) - 1
         self.qn = [int(x) for x in q_]
         desc = MpoDesc(self.L, len(q_), _ptr(q_, _ip), _ptr(D_, _ip), _ptr(f_, _ip), _ptr(W_, _dp), int(qtot))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        cfg = Config(prec, int(kmax), C.c_void_p(stream))
+        cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)))
         h = C.c_void_p()
         _check(lib().dmrg_init_mpo(C.byref(h), C.byref(desc), C.byref(cfg)))
         self._h = h
@@ -294,6 +298,21 @@ class Engine:
         n = C.c_int(0)
         _check(lib().dmrg_get_lambda(self._h, int(b), _ptr(v, _dp), 65536, C.byref(n)), self._h)
         return v[: n.value].copy()
+
+    def site(self, j):
+        n = C.c_longlong(0)
+        st = lib().dmrg_get_site(self._h, int(j), None, 0, C.byref(n))
+        if st not in (0, 4):
+            _check(st, self._h)
+        v = np.zeros(max(1, n.value))
+        _check(lib().dmrg_get_site(self._h, int(j), _ptr(v, _dp), v.size, C.byref(n)), self._h)
+        return v[: n.value].copy()
+
+    def state(self):
+        """(bonds, packed site data, centre) of the serial state, for set_mps."""
+        bonds = [self.bond(b) for b in range(self.L + 1)]
+        data = np.concatenate([self.site(j) for j in range(self.L)])
+        return bonds, data, self.center()
 
     def center(self, region=0):
         s = C.c_int(0)

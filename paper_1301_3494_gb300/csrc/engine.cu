@@ -94,6 +94,7 @@ struct dmrg_ctx {
     std::vector<SiteMPO> W;
     std::vector<std::unique_ptr<TwoSiteMPO>> w12;   // per bond (j, j+1), lazily built
     int prec = DMRG_FP64, kmax = 8;
+    bool svd_fp64 = false;       // mixed modes: FP64 splits on ordinary bonds too
     cudaStream_t base = nullptr;
     std::unique_ptr<Chain> serial;
     std::vector<std::unique_ptr<Chain>> reg;
@@ -208,7 +209,7 @@ void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_
     A.ensure(std::max<long long>(1, na) * 8, st);
     B.ensure(std::max<long long>(1, nb) * 8, st);
     // mixed-precision modes: FP32 Jacobi on ordinary bonds; FP64 at shared (accurate) bonds
-    const bool fp32 = c->prec != DMRG_FP64 && !accurate;
+    const bool fp32 = c->prec != DMRG_FP64 && !accurate && !c->svd_fp64;
     SplitResult r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
                               right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st, fp32);
     if (fp32) {
@@ -673,6 +674,7 @@ dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_c
     C->qn.assign(mpo->qn_local, mpo->qn_local + mpo->d);
     C->prec = cfg->precision;
     C->kmax = cfg->kmax > 0 ? cfg->kmax : 8;
+    C->svd_fp64 = cfg->svd_fp64 != 0;
     PD_REQUIRE(C->kmax >= 2 && C->kmax <= 32, DMRG_ERR_ARG, "kmax must be in [2, 32]");
     C->base = (cudaStream_t)cfg->stream;
     PD_REQUIRE(mpo->D[0] == 1 && mpo->D[C->L] == 1, DMRG_ERR_ARG, "D[0] and D[L] must be 1");
@@ -876,6 +878,20 @@ dmrg_status dmrg_get_lambda(dmrg_ctx* c, int b, double* lam, int cap, int* n) {
     *n = (int)v.size();
     PD_REQUIRE((int)v.size() <= cap && lam, DMRG_ERR_CAPACITY, "capacity too small");
     for (size_t i = 0; i < v.size(); ++i) lam[i] = v[i];
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_get_site(dmrg_ctx* c, int j, double* out, long long cap, long long* n) {
+    CTX_TRY
+    PD_REQUIRE(c && n && c->have_state && j >= 0 && j < c->L, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->reg.empty(), DMRG_ERR_STATE, "site export needs a serial state");
+    Chain& ch = *c->serial;
+    const SiteLayout S = site_layout(ch.bond[j], ch.bond[j + 1], c->qn);
+    *n = S.size;
+    PD_REQUIRE(S.size <= cap && out, DMRG_ERR_CAPACITY, "capacity too small");
+    if (S.size) PD_CK(cudaMemcpyAsync(out, ch.site[j].p, S.size * 8, cudaMemcpyDeviceToHost, ch.st));
+    PD_CK(cudaStreamSynchronize(ch.st));
     return DMRG_OK;
     CTX_CATCH(c)
 }

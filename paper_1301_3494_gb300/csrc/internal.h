@@ -52,8 +52,8 @@ void* prof_start(cudaStream_t st);
 void prof_stop(void* token, cudaStream_t st, int cls, double flops);
 // Jacobi SVD statistics (sweeps run per call), accumulated while profiling is on; kind 0: FP32
 // scalar Jacobi, 1: FP32 block Jacobi, 2: FP64; max_rows: the call's largest sector row count;
-// flops: the FP32 Gram and rotation flops of a block-Jacobi call.
-void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops);
+// flops: the FP32 Gram and rotation flops of a block-Jacobi call; rot_hist: its rotations per sweep.
+void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist);
 // An FP32 split redone in FP64 (counted always, not only while profiling).
 void prof_fallback();
 

@@ -1324,32 +1324,29 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it; the
         // kept factor that joins a block is re-orthonormalised in FP64 afterwards
         const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)maxp));
-        {
-            // block Jacobi: one task per block pair, n / 16 - 1 rounds per sweep
-            std::vector<BjSec> bs(nsec);
-            std::vector<int> task_sec;
-            int nrounds = 0;
-            for (int s = 0; s < nsec; ++s) {
-                BjSec b{};
-                b.nb = (ss[s].n + 15) / 16;
-                b.nbp = b.nb + (b.nb & 1);
-                b.task0 = (int)task_sec.size();
-                b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
-                for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
-                if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
-                bs[s] = b;
-            }
-            DBuf dbs, dts, dgmax;
-            upload(dbs, bs, st);
-            upload(dts, task_sec, st);
-            dgmax.ensure(std::max(1, nsec) * 4, st);
-            PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
-            PD_CK(cudaMemsetAsync(dflops.p, 0, 8, st));
-            launch_bjacobi(dsecs.as<SvdSec>(), dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, maxp, maxn, 40,
-                           2, dW.as<float>(), dV.as<float>(), tol, 8.0f * FLT_EPSILON, dgmax.as<float>(),
-                           drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr,
-                           dflops.as<unsigned long long>(), st);
+        // block Jacobi: one task per block pair, n / 16 - 1 rounds per sweep
+        std::vector<BjSec> bs(nsec);
+        std::vector<int> task_sec;
+        int nrounds = 0;
+        for (int s = 0; s < nsec; ++s) {
+            BjSec b{};
+            b.nb = (ss[s].n + 15) / 16;
+            b.nbp = b.nb + (b.nb & 1);
+            b.task0 = (int)task_sec.size();
+            b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
+            for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
+            if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
+            bs[s] = b;
         }
+        DBuf dbs, dts, dgmax;
+        upload(dbs, bs, st);
+        upload(dts, task_sec, st);
+        dgmax.ensure(std::max(1, nsec) * 4, st);
+        PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
+        PD_CK(cudaMemsetAsync(dflops.p, 0, 8, st));
+        launch_bjacobi(dsecs.as<SvdSec>(), dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, maxp, maxn, 40,
+                       2, dW.as<float>(), dV.as<float>(), tol, 8.0f * FLT_EPSILON, dgmax.as<float>(), drot.as<int>(),
+                       drot.as<int>() + max_sweeps, bar, jerr, dflops.as<unsigned long long>(), st);
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
         run_copy<double>(gather, psi, dW.p, Num::F64, st);
@@ -1372,12 +1369,14 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         PD_CK(cudaEventRecord(sv1, st));
         int sweeps = 0;
         unsigned long long fl = 0;
+        std::vector<int> hist(max_sweeps, 0);
         PD_CK(cudaMemcpyAsync(&sweeps, drot.as<int>() + max_sweeps, 4, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaMemcpyAsync(hist.data(), drot.p, 4 * max_sweeps, cudaMemcpyDeviceToHost, st));
         if (fp32) PD_CK(cudaMemcpyAsync(&fl, dflops.p, 8, cudaMemcpyDeviceToHost, st));
         PD_CK(cudaStreamSynchronize(st));
         float ms = 0.f;
         PD_CK(cudaEventElapsedTime(&ms, sv0, sv1));
-        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl);
+        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl, fp32 ? hist.data() : nullptr, max_sweeps);
         cudaEventDestroy(sv0);
         cudaEventDestroy(sv1);
     }

@@ -46,6 +46,7 @@ std::atomic<bool> g_on{false};
 std::vector<Rec> g_pending;
 long long g_svd_calls = 0, g_svd_sweeps = 0, g_svd_block = 0, g_svd_f64 = 0, g_svd_rows = 0;
 double g_svd_ms = 0.0, g_svd_block_ms = 0.0, g_svd_f64_ms = 0.0, g_svd_block_flops = 0.0;
+long long g_rot_hist[48] = {0};
 double g_ms[4] = {0, 0, 0, 0}, g_fl[4] = {0, 0, 0, 0};
 long long g_n[4] = {0, 0, 0, 0};
 }  // namespace
@@ -70,7 +71,7 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops) {
     delete[] ev;
 }
 
-void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops) {
+void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_svd_calls += 1;
     g_svd_sweeps += sweeps;
@@ -78,6 +79,7 @@ void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops) {
     if (kind == 1) g_svd_block += 1, g_svd_block_ms += ms, g_svd_block_flops += flops;
     if (kind == 2) g_svd_f64 += 1, g_svd_f64_ms += ms;
     g_svd_rows = std::max<long long>(g_svd_rows, max_rows);
+    for (int i = 0; rot_hist && i < nhist && i < 48; ++i) g_rot_hist[i] += rot_hist[i];
 }
 
 }  // namespace pd
@@ -99,6 +101,7 @@ void dmrg_profile_reset(void) {
     for (int i = 0; i < 4; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
     g_svd_calls = g_svd_sweeps = g_svd_block = g_svd_f64 = g_svd_rows = 0;
     g_svd_ms = g_svd_block_ms = g_svd_f64_ms = g_svd_block_flops = 0.0;
+    for (auto& x : g_rot_hist) x = 0;
     g_launches.store(0);
     g_fallbacks.store(0);
 }
@@ -141,6 +144,7 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->svd_max_rows = g_svd_rows;
     out->svd_fp64_fallbacks = g_fallbacks.load();
     out->svd_block_flops = g_svd_block_flops;
+    for (int i = 0; i < 48; ++i) out->svd_rot_hist[i] = g_rot_hist[i];
     return DMRG_OK;
 }
 

@@ -145,3 +145,23 @@ def test_mixed_precision_regions_within_1e5():
     for m in (32, 64, 64, 64, 64):
         g = eng.sweep(m, dav_tol=1e-9, dav_max_iter=12, refine_iters=6)
     assert abs(g["energy"] - r["energy"]) <= 1e-5 * abs(r["energy"]), (g["energy"], r["energy"])
+
+
+def test_state_export_round_trip():
+    """dmrg_get_site / dmrg_get_bond / dmrg_get_center reproduce the state through dmrg_set_mps:
+    a second engine built from the export has the same FP64 energy and the same bond tables."""
+    L = 16
+    mpo = wl.heisenberg_chain(L)
+    mps = wl.random_mps(L, mpo.site.qn, 0, 8, seed=3)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, mps, list(mpo.site.qn))
+    for m in (16, 32):
+        eng.sweep(m)
+    bonds, data, c = eng.state()
+    e1 = eng.energy()
+    eng2 = engine_for(pd, mpo)
+    eng2.set_mps(bonds, data, center=c)
+    assert abs(eng2.energy() - e1) <= 1e-12 * abs(e1)
+    assert all(eng2.bond(b) == bonds[b] for b in range(L + 1))
+    eng.close()
+    eng2.close()
