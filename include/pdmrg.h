@@ -191,6 +191,17 @@ dmrg_status dmrg_get_bond(dmrg_ctx* ctx, int b, int* q_out, int* m_out, int cap,
  * sectors ascending, normalised to sum lambda^2 = 1).  *n_out = count. */
 dmrg_status dmrg_get_lambda(dmrg_ctx* ctx, int b, double* lam_out, int cap, int* n_out);
 
+/* Gradient of the energy E = <Psi|H|Psi>/<Psi|Psi> of the serial state with respect to every
+ * MPO tensor (FP64 contexts; no counterpart in the paper): Wbar (host, caller owned) receives the
+ * tensors dE/dW_j in the layout of dmrg_mpo_desc.W (site after site, [D_j][d][d][D_{j+1}]),
+ * exact at the nonzero entries of the MPO and zero elsewhere.  For a variationally optimised
+ * state, dE/dtheta = sum_j <Wbar_j, dW_j/dtheta> for any MPO parameter theta (Hellmann-Feynman).
+ * One gauge sweep: at each bond the backward of the projected Hamiltonian with ybar = psi gives
+ * the gradient of the left site (the last bond also the right one); the centre is moved by
+ * untruncated SVDs and returned to site 0.  E_out (nullable): <psi|H_eff|psi> at the last bond.
+ * Region mode or mixed precision: DMRG_ERR_STATE. */
+dmrg_status dmrg_energy_gradient(dmrg_ctx* ctx, double* Wbar, double* E_out);
+
 /* Site tensor j of the serial state (checkpointing): the packed layout of dmrg_set_mps for
  * bonds (j, j + 1) as dmrg_get_bond reports them, copied to host memory out[cap] (FP64, caller
  * owned); *n_out = its element count (DMRG_ERR_CAPACITY, with *n_out set, if cap is smaller).
@@ -293,6 +304,20 @@ dmrg_status dmrg_heff_apply_noalloc(const dmrg_bond_desc* bd, const double* L_de
  * tensor (D2, f2, W2 unused). */
 dmrg_status dmrg_env_left(const dmrg_bond_desc* bd, int prec, const double* Lin_dev,
                           const double* A_dev, double* Lout_dev, void* stream);
+
+/* Backward of the H_eff application (FP64; no counterpart in the paper, which has no
+ * derivatives): given ybar = dPhi/dy for y = H_eff(L, W1, W2, R) x, the gradients
+ *   xbar[a,s1',s2',c] = sum ybar[a',s1,s2,c'] L[a',w,a] W1[w,s1,s1',w'] W2[w',s2,s2',w''] R[c',w'',c]
+ *   Lbar[a',w,a], Rbar[c',w'',c]  (packed environment layouts of the bond descriptor)
+ *   W1bar[w,s1,s1',w'], W2bar[w',s2,s2',w''] (dense, host, nullable; exact at every nonzero entry
+ *   of W1 / W2, zero elsewhere: the MPO's sparsity pattern is fixed)
+ * x, ybar, xbar: packed two-site layout; L, R, Lbar, Rbar: packed environments (device, caller
+ * owned, outputs overwritten).  The forward intermediates are recomputed from x.  Synchronises
+ * the stream. */
+dmrg_status dmrg_heff_backward(const dmrg_bond_desc* bd, const double* L_dev, const double* R_dev,
+                               const double* x_dev, const double* ybar_dev, double* xbar_dev,
+                               double* Lbar_dev, double* Rbar_dev, double* W1bar, double* W2bar,
+                               void* stream);
 
 /* Right-environment update (operator transformation by B):
  * Rout[a',w,a] = sum B[a',s,c'] Rin[c',w',c] W[w,s,s',w'] B[a,s',c]. */

@@ -117,17 +117,21 @@ def lib():
         L.dmrg_get_lambda.argtypes = [vp, C.c_int, _dp, C.c_int, _ip]
         L.dmrg_get_center.argtypes = [vp, C.c_int, _ip]
         L.dmrg_get_site.argtypes = [vp, C.c_int, _dp, C.c_longlong, C.POINTER(C.c_longlong)]
+        L.dmrg_energy_gradient.argtypes = [vp, _dp, _dp]
         L.dmrg_destroy.argtypes = [vp]
         L.dmrg_heff_apply.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp, _dp, vp]
         L.dmrg_heff_apply_noalloc.argtypes = [C.POINTER(BondDesc), vp, vp, vp, vp, vp]
+        L.dmrg_heff_backward.argtypes = [C.POINTER(BondDesc), vp, vp, vp, vp, vp, vp, vp, _dp, _dp, vp]
         L.dmrg_env_left.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
         L.dmrg_env_right.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
         L.dmrg_svd_split.argtypes = [C.POINTER(BondDesc), vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, _ip, _ip, _ip,
                                      _dp, vp]
         for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
                      "dmrg_profile_read", "dmrg_merge",
-                     "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_get_site", "dmrg_destroy",
-                     "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_env_left", "dmrg_env_right",
+                     "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_get_site",
+                     "dmrg_energy_gradient", "dmrg_destroy",
+                     "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_heff_backward", "dmrg_env_left",
+                     "dmrg_env_right",
                      "dmrg_svd_split"):
             getattr(L, name).restype = st
         _lib = L
@@ -204,6 +208,16 @@ def heff_apply_noalloc(bond: Bond, L_dev, R_dev, x_dev, y_dev, stream=0):
     _check(lib().dmrg_heff_apply_noalloc(C.byref(bond.desc), L_dev, R_dev, x_dev, y_dev, stream))
 
 
+def heff_backward(bond: Bond, L_dev, R_dev, x_dev, ybar_dev, xbar_dev, Lbar_dev, Rbar_dev, want_w=True, stream=0):
+    """Gradients of Phi for y = H_eff x given ybar = dPhi/dy (FP64): writes xbar, Lbar, Rbar
+    (device) and returns (W1bar, W2bar) as dense numpy arrays (or (None, None))."""
+    W1b = np.zeros(bond.W1.shape) if want_w else None
+    W2b = np.zeros(bond.W2.shape) if want_w else None
+    _check(lib().dmrg_heff_backward(C.byref(bond.desc), L_dev, R_dev, x_dev, ybar_dev, xbar_dev, Lbar_dev, Rbar_dev,
+                                    _ptr(W1b, _dp) if want_w else None, _ptr(W2b, _dp) if want_w else None, stream))
+    return W1b, W2b
+
+
 def env_left(bond: Bond, prec, Lin_dev, A_dev, Lout_dev, stream=0):
     _check(lib().dmrg_env_left(C.byref(bond.desc), int(prec), Lin_dev, A_dev, Lout_dev, stream))
 
@@ -235,6 +249,7 @@ class Engine:
         W_, f_, D_, q_ = self._keep
         self.L = len(D_) - 1
         self.qn = [int(x) for x in q_]
+        self._wshapes = [(int(D_[j]), len(q_), len(q_), int(D_[j + 1])) for j in range(self.L)]
         desc = MpoDesc(self.L, len(q_), _ptr(q_, _ip), _ptr(D_, _ip), _ptr(f_, _ip), _ptr(W_, _dp), int(qtot))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)))
@@ -307,6 +322,19 @@ class Engine:
         v = np.zeros(max(1, n.value))
         _check(lib().dmrg_get_site(self._h, int(j), _ptr(v, _dp), v.size, C.byref(n)), self._h)
         return v[: n.value].copy()
+
+    def energy_gradient(self):
+        """(dE/dW_j for every site j as arrays shaped like the MPO tensors, E)."""
+        shapes = self._wshapes
+        Wb = np.zeros(sum(int(np.prod(sh)) for sh in shapes))
+        e = C.c_double(0.0)
+        _check(lib().dmrg_energy_gradient(self._h, _ptr(Wb, _dp), C.byref(e)), self._h)
+        out, off = [], 0
+        for sh in shapes:
+            k = int(np.prod(sh))
+            out.append(Wb[off: off + k].reshape(sh))
+            off += k
+        return out, e.value
 
     def state(self):
         """(bonds, packed site data, centre) of the serial state, for set_mps."""

@@ -882,6 +882,52 @@ dmrg_status dmrg_get_lambda(dmrg_ctx* c, int b, double* lam, int cap, int* n) {
     CTX_CATCH(c)
 }
 
+dmrg_status dmrg_energy_gradient(dmrg_ctx* c, double* Wbar, double* E) {
+    CTX_TRY
+    PD_REQUIRE(c && Wbar && c->have_state, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->reg.empty(), DMRG_ERR_STATE, "the energy gradient needs a serial state");
+    PD_REQUIRE(c->prec == DMRG_FP64, DMRG_ERR_STATE, "the energy gradient runs in FP64 mode");
+    Chain& ch = *c->serial;
+    const int L = c->L;
+    cudaStream_t st = ch.st;
+    // move the centre to site 0 by untruncated SVDs
+    while (ch.oc > 0) gauge_step(c, ch, ch.oc - 1, false);
+    std::vector<size_t> off(L + 1, 0);
+    for (int j = 0; j < L; ++j) off[j + 1] = off[j] + c->W[j].W.size();
+    double e_acc = 0.0;
+    for (int j = 0; j + 1 < L; ++j) {
+        DBuf psi;
+        form_psi(c, ch, j, psi);
+        const long long n = psi_layout(ch.bond[j], ch.bond[j + 2], c->qn).size;
+        const double nrm2 = dot_host(psi.as<double>(), psi.as<double>(), n, st);
+        PD_REQUIRE(nrm2 > 0.0, DMRG_ERR_NUMERIC, "zero two-site wavefunction");
+        scale_vec(psi.as<double>(), n, 1.0 / std::sqrt(nrm2), st);
+        const EnvSlab& Le = *ch.Lenv[j];
+        const EnvSlab& Re = *ch.Renv[j + 2];
+        DBuf Lp, Rp, xb, Lb, Rb;
+        Lp.ensure(std::max<long long>(1, Le.lay.packed_size) * 8, st);
+        Rp.ensure(std::max<long long>(1, Re.lay.packed_size) * 8, st);
+        Lb.ensure(std::max<long long>(1, Le.lay.packed_size) * 8, st);
+        Rb.ensure(std::max<long long>(1, Re.lay.packed_size) * 8, st);
+        xb.ensure(std::max<long long>(1, n) * 8, st);
+        env_to_packed(Le, Lp.as<double>(), st);
+        env_to_packed(Re, Rp.as<double>(), st);
+        // Phi = <psi, H_eff psi>: with ybar = psi the MPO gradient of site j is dE/dW_j (the other
+        // sites sit in the environments); the last bond also gives site L - 1
+        heff_backward(ch.bond[j], ch.bond[j + 2], c->qn, c->W[j], c->W[j + 1], Lp.as<double>(), Rp.as<double>(),
+                      psi.as<double>(), psi.as<double>(), xb.as<double>(), Lb.as<double>(), Rb.as<double>(),
+                      Wbar + off[j], j + 2 == L ? Wbar + off[j + 1] : nullptr, st);
+        // xbar = H_eff^T psi, so <psi, xbar> = <psi|H_eff|psi>
+        e_acc = dot_host(psi.as<double>(), xb.as<double>(), n, st);
+        if (j + 2 < L) gauge_step(c, ch, j, true);
+    }
+    // back to site 0
+    while (ch.oc > 0) gauge_step(c, ch, ch.oc - 1, false);
+    if (E) *E = e_acc;
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
 dmrg_status dmrg_get_site(dmrg_ctx* c, int j, double* out, long long cap, long long* n) {
     CTX_TRY
     PD_REQUIRE(c && n && c->have_state && j >= 0 && j < c->L, DMRG_ERR_ARG, "bad argument");

@@ -300,6 +300,14 @@ void form_two_site(const Sec& bl, const Sec& bm, const Sec& br, const std::vecto
                    const double* left, const double* right, const double* mid, double* psi,
                    cudaStream_t st);
 
+// Backward of the FP64 H_eff application on packed operands (L, R packed environments of the
+// bonds bl / br for the MPO fluxes of w1 / w2): xbar, Lbar, Rbar (device) and W1bar, W2bar (dense
+// host arrays, nullable) for ybar = dPhi/dy.  Synchronises the stream.
+void heff_backward(const Sec& bl, const Sec& br, const std::vector<int>& qn, const SiteMPO& w1, const SiteMPO& w2,
+                   const double* L_dev, const double* R_dev, const double* x_dev, const double* ybar_dev,
+                   double* xbar_dev, double* Lbar_dev, double* Rbar_dev, double* W1bar, double* W2bar,
+                   cudaStream_t st);
+
 // SVD split of a packed two-site wavefunction.
 struct SplitResult {
     Sec mid;                      // kept sectors of the new middle bond
