@@ -51,13 +51,16 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy"], default="sweeps",
+    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy", "grad"], default="sweeps",
                     help="sweeps: a step is one real-space parallel sweep (Fig. 4) over the whole lattice; "
                          "steps: a step is one bulk two-site update (serial); op: repeated H_eff matvecs at "
                          "one bond (random environments, small device footprint, for profiler captures); "
                          "accuracy: the same serial sweeps (m ramped to --acc-m) in FP64 and in --precision "
                          "mode from the same seeded state, energies and sweep times compared")
     ap.add_argument("--acc-m", type=int, default=500)
+    ap.add_argument("--grad-L", type=int, default=128)
+    ap.add_argument("--grad-m", type=int, default=128)
+    ap.add_argument("--grad-jq-m", type=int, default=128)
     ap.add_argument("--acc-sweeps", type=int, default=6)
     ap.add_argument("--acc-variants", default="",
                     help="accuracy: extra same-state sweeps, comma-separated precision:refine_iters[:svd64][:davN] "
@@ -190,6 +193,82 @@ def accuracy_mode(args):
            "separate_runs": {"E_fp64": e64, "E_mixed": emx, "dE_over_E": abs(emx - e64) / abs(e64)},
            "variants": {k: dict(v, dE_over_E=abs(v["E_after_sweep"] - s64) / abs(s64)) for k, v in same.items()},
            "E_per_site_fp64": s64 / L, "detail": res}
+    print(json.dumps(out))
+
+
+def grad_mode(args):
+    """Energy derivatives from the library's gradient (Hellmann-Feynman through dmrg_energy_gradient)
+    against central finite differences of converged DMRG energies (step 1e-4) and, for the
+    transverse-field Ising chain, the free-fermion closed form; J-Q2 16x8 cylinder: dE/dQ for a
+    global scale of the plaquette couplings."""
+    import torch
+    import paper_1301_3494_gb300 as pd
+    out = {"mode": "grad", "tfim": [], "jq2": None}
+
+    def tfim_exact(L_, J_, h_):
+        # open chain as free fermions: E0 = -sum of the singular values of the L x L bidiagonal
+        # matrix with h on the diagonal and J above it
+        M = np.diag(np.full(L_, float(h_))) + np.diag(np.full(L_ - 1, float(J_)), 1)
+        return -float(np.sum(np.linalg.svd(M, compute_uv=False)))
+
+    def converge(mpo, m, sweeps=6, seed=2):
+        W, flux, D = wl.pack_mpo(mpo)
+        qn = list(mpo.site.qn)
+        eng = pd.Engine(W, flux, D, qn, mpo.qtot, "fp64", args.kmax)
+        mps = wl.random_mps(mpo.L, qn, mpo.qtot, min(16, m), seed=seed)
+        data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(mpo.L)])
+        eng.set_mps(mps.bonds, data)
+        ramp = [min(m, 16 * 2 ** k) for k in range(sweeps)]
+        ramp[-2:] = [m, m]
+        for mm in ramp:
+            eng.sweep(mm, dav_tol=1e-10, dav_max_iter=40)
+        torch.cuda.synchronize()
+        return eng
+
+    def directional(Wbar, Wp, Wm, step):
+        return sum(float(np.sum(g * (a - b))) / (2 * step) for g, a, b in zip(Wbar, Wp.W, Wm.W))
+
+    L, m, fd = args.grad_L, args.grad_m, 1e-4
+    for h in (0.5, 1.0, 1.5):
+        t0 = time.perf_counter()
+        eng = converge(wl.tfim_chain(L, 1.0, h), m)
+        Wbar, e = eng.energy_gradient()
+        eng.close()
+        dh = directional(Wbar, wl.tfim_chain(L, 1.0, h + fd), wl.tfim_chain(L, 1.0, h - fd), fd)
+        dJ = directional(Wbar, wl.tfim_chain(L, 1.0 + fd, h), wl.tfim_chain(L, 1.0 - fd, h), fd)
+        ep = converge(wl.tfim_chain(L, 1.0, h + fd), m)
+        em = converge(wl.tfim_chain(L, 1.0, h - fd), m)
+        fd_h = (ep.energy() - em.energy()) / (2 * fd)
+        ep.close()
+        em.close()
+        st = 1e-5
+        exact_h = (tfim_exact(L, 1.0, h + st) - tfim_exact(L, 1.0, h - st)) / (2 * st)
+        exact_J = (tfim_exact(L, 1.0 + st, h) - tfim_exact(L, 1.0 - st, h)) / (2 * st)
+        out["tfim"].append({"L": L, "m": m, "h": h, "E": e, "E_exact": tfim_exact(L, 1.0, h),
+                            "dE_dh_gradient": dh, "dE_dh_fd": fd_h, "dE_dh_exact": exact_h,
+                            "dE_dJ_gradient": dJ, "dE_dJ_exact": exact_J,
+                            "rel_err_dh_vs_exact": abs(dh - exact_h) / abs(exact_h),
+                            "rel_err_dJ_vs_exact": abs(dJ - exact_J) / abs(exact_J),
+                            "rel_err_dh_vs_fd": abs(dh - fd_h) / abs(fd_h), "seconds": time.perf_counter() - t0})
+    # J-Q2 16x8: dE/dQ for Q_p -> s Q_p at s = 1
+    t0 = time.perf_counter()
+    mpo, Jc, Qc = wl.jq2_cylinder(16, 8, seed=1)
+    mj = args.grad_jq_m
+
+    def jq(sc):
+        terms, _ = wl.jq2_terms(16, 8, Jc, Qc * sc)
+        return wl.build_mpo(16 * 8, wl.spin_half(), terms)
+
+    eng = converge(mpo, mj)
+    Wbar, e = eng.energy_gradient()
+    eng.close()
+    dQ = directional(Wbar, jq(1 + fd), jq(1 - fd), fd)
+    ep, em = converge(jq(1 + fd), mj), converge(jq(1 - fd), mj)
+    fd_Q = (ep.energy() - em.energy()) / (2 * fd)
+    ep.close()
+    em.close()
+    out["jq2"] = {"lattice": "16x8 cylinder", "m": mj, "D": max(mpo.D), "E": e, "dE_dQscale_gradient": dQ,
+                  "dE_dQscale_fd": fd_Q, "rel_diff": abs(dQ - fd_Q) / abs(fd_Q), "seconds": time.perf_counter() - t0}
     print(json.dumps(out))
 
 
@@ -410,6 +489,9 @@ def main():
         return
     if args.mode == "accuracy":
         accuracy_mode(args)
+        return
+    if args.mode == "grad":
+        grad_mode(args)
         return
     W, flux, D = wl.pack_mpo(mpo)
     eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
