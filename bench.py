@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16", "tf32", "fp64"], default="bf16")
+    ap.add_argument("--lattice", choices=["square", "triangular"], default="square",
+                    help="Heisenberg cylinder of the sweeps/steps modes (triangular adds the (x,y)-(x+1,y-1) bonds)")
     ap.add_argument("--lx", type=int, default=24)
     ap.add_argument("--ly", type=int, default=8)
     ap.add_argument("--m", type=int, default=2000)
@@ -51,7 +53,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy", "grad"], default="sweeps",
+    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy", "grad", "chain"], default="sweeps",
                     help="sweeps: a step is one real-space parallel sweep (Fig. 4) over the whole lattice; "
                          "steps: a step is one bulk two-site update (serial); op: repeated H_eff matvecs at "
                          "one bond (random environments, small device footprint, for profiler captures); "
@@ -59,6 +61,12 @@ def parse():
                          "mode from the same seeded state, energies and sweep times compared")
     ap.add_argument("--acc-m", type=int, default=500)
     ap.add_argument("--grad-L", type=int, default=128)
+    ap.add_argument("--chain-L", type=int, default=200)
+    ap.add_argument("--chain-ramp", default="64,64,128,128,256,256,512,512")
+    ap.add_argument("--chain-spin", choices=["half", "one"], default="half")
+    ap.add_argument("--chain-warmup", type=int, default=0)
+    ap.add_argument("--chain-runs", default="",
+                    help="chain: runs to make, comma-separated precision[:svd64] (default: fp64 and --precision)")
     ap.add_argument("--grad-m", type=int, default=128)
     ap.add_argument("--grad-jq-m", type=int, default=128)
     ap.add_argument("--acc-sweeps", type=int, default=6)
@@ -272,8 +280,54 @@ def grad_mode(args):
     print(json.dumps(out))
 
 
+def chain_mode(args):
+    """Heisenberg chain with R real-space regions (the paper's Fig. 3 / 200-site setting): the same
+    m ramp of parallel sweeps in FP64 and in --precision mode from the same seeded state; per sweep
+    the energy, the merge prediction fidelities 1 - |<Psi'|Psi>| and the sweep seconds; the final
+    states' energies evaluated with FP64 environments and compared."""
+    import torch
+    import paper_1301_3494_gb300 as pd
+    L = args.chain_L
+    mpo = wl.heisenberg_chain(L, spin=args.chain_spin)
+    qn = list(mpo.site.qn)
+    W, flux, D = wl.pack_mpo(mpo)
+    mps = wl.random_mps(L, qn, 0, 16, seed=args.seed)
+    data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
+    ramp = [int(x) for x in args.chain_ramp.split(",")]
+    res = {}
+    finals = {}
+    runs = [r for r in args.chain_runs.split(",") if r] or ["fp64", args.precision]
+    for run in runs:
+        prec = run.split(":")[0]
+        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax, svd_fp64=run.endswith(":svd64"))
+        eng.set_mps(mps.bonds, data)
+        dav = dict(dav_tol=1e-9, dav_max_iter=12, refine_iters=0 if prec == "fp64" else 6, serial_regions=1)
+        t0 = time.perf_counter()
+        eng.setup_regions(args.regions, args.chain_warmup, ramp[0], **dav)
+        t_setup = time.perf_counter() - t0
+        rows = []
+        for m in ramp:
+            t0 = time.perf_counter()
+            g = eng.sweep(m, **dav)
+            torch.cuda.synchronize()
+            rows.append({"m": m, "energy": g["energy"], "fidelity_min": g["min_fidelity"],
+                         "fidelity_max": g["max_fidelity"], "max_trunc_err": g["max_trunc_err"],
+                         "sweep_s": time.perf_counter() - t0})
+        res[run] = {"setup_s": t_setup, "sweeps": rows}
+        finals[run] = rows[-1]["energy"]
+        eng.close()
+    out = {"mode": "chain", "L": L, "spin": args.chain_spin, "regions": args.regions, "warmup": args.chain_warmup,
+           "m_ramp": ramp, "final_energies": finals, "detail": res}
+    if "fp64" in finals and args.precision in finals:
+        out["dE_over_E_last_merge"] = abs(finals[args.precision] - finals["fp64"]) / abs(finals["fp64"])
+    print(json.dumps(out))
+
+
 def workload(args):
-    mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
+    if args.lattice == "triangular":
+        mpo = wl.heisenberg_triangular_cylinder(args.lx, args.ly)
+    else:
+        mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
     qn = list(mpo.site.qn)
     L = mpo.L
     if args.mode == "sweeps":
@@ -447,7 +501,7 @@ def main():
     rank, world, dist = dist_init(args)
     mpo, qn, mps, center = workload(args)
     L = mpo.L
-    workload_name = f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}"
+    workload_name = f"heisenberg_{args.lattice}_cylinder_{args.lx}x{args.ly}_m{args.m}"
     if args.impl == "reference":
         if rank != 0:
             return
@@ -467,7 +521,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_m{args.m}",
+            "config": {"workload": f"heisenberg_{args.lattice}_cylinder_{args.lx}x{args.ly}_m{args.m}",
                        "D": max(mpo.D), "m": args.m, "bond": sample_bond, "precision": "fp64-oracle"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": f"one full H_eff matvec of the CPU oracle per step at bond {sample_bond} "
@@ -492,6 +546,9 @@ def main():
         return
     if args.mode == "grad":
         grad_mode(args)
+        return
+    if args.mode == "chain":
+        chain_mode(args)
         return
     W, flux, D = wl.pack_mpo(mpo)
     eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
