@@ -354,7 +354,11 @@ def right_canonicalize(mps_sites, bonds, qn):
             for s, qr in cols:
                 newblk[(ql, s)] = Vt[:, c0: c0 + br[qr]].copy()
                 c0 += br[qr]
-            carry[ql] = U * S
+            carry[ql] = (U, S)
+        # the overall scale is irrelevant (the state is normalised at the end); dividing each
+        # carry by the norm of its singular values keeps long random chains from overflowing
+        nrm_j = np.sqrt(sum(float(np.sum(S * S)) for _, S in carry.values()))
+        carry = {q: U * (S / nrm_j) for q, (U, S) in carry.items()}
         sites[j] = newblk
         bonds[j] = newdims
         prev = {}
