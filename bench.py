@@ -53,13 +53,16 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy", "grad", "chain"], default="sweeps",
+    ap.add_argument("--mode", choices=["steps", "sweeps", "op", "accuracy", "grad", "chain", "observe"],
+                    default="sweeps",
                     help="sweeps: a step is one real-space parallel sweep (Fig. 4) over the whole lattice; "
                          "steps: a step is one bulk two-site update (serial); op: repeated H_eff matvecs at "
                          "one bond (random environments, small device footprint, for profiler captures); "
                          "accuracy: the same serial sweeps (m ramped to --acc-m) in FP64 and in --precision "
                          "mode from the same seeded state, energies and sweep times compared")
     ap.add_argument("--acc-m", type=int, default=500)
+    ap.add_argument("--obs-m", type=int, default=800,
+                    help="observe: bond dimension of the seeded state put in the inverse canonical gauge")
     ap.add_argument("--grad-L", type=int, default=128)
     ap.add_argument("--chain-L", type=int, default=200)
     ap.add_argument("--chain-ramp", default="64,64,128,128,256,256,512,512")
@@ -277,6 +280,67 @@ def grad_mode(args):
     em.close()
     out["jq2"] = {"lattice": "16x8 cylinder", "m": mj, "D": max(mpo.D), "E": e, "dE_dQscale_gradient": dQ,
                   "dE_dQscale_fd": fd_Q, "rel_diff": abs(dQ - fd_Q) / abs(fd_Q), "seconds": time.perf_counter() - t0}
+    print(json.dumps(out))
+
+
+def observe_mode(args):
+    """Inverse canonical gauge (Sec. IV) of a seeded --lx x --ly cylinder state with bond dimension
+    --obs-m, then every one- and nearest-neighbour two-site expectation value over the whole lattice
+    in one measurement pass (dmrg_local_expectations), timed over --steps passes after --warmup.
+    Checks that hold at any size: the S^z sum rule of the sector and, on sampled sites, that psi_j
+    carries the Schmidt weights of both its bonds (psi_j is an orthogonality centre)."""
+    import torch
+    import paper_1301_3494_gb300 as pd
+    mpo = wl.heisenberg_square_cylinder(args.lx, args.ly)
+    qn = list(mpo.site.qn)
+    L = mpo.L
+    W, flux, D = wl.pack_mpo(mpo)
+    eng = pd.Engine(W, flux, D, qn, mpo.qtot, "fp64", args.kmax)
+    mps = wl.random_mps(L, qn, mpo.qtot, args.obs_m, seed=args.seed, sigma=args.sigma)
+    data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
+    eng.set_mps(mps.bonds, data)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eng.inverse_canonical()
+    torch.cuda.synchronize()
+    gauge_s = time.perf_counter() - t0
+    st = mpo.site
+    Sz, Sp, Sm, I2 = st.op("Sz"), st.op("Sp"), st.op("Sm"), np.eye(st.d)
+    ops1 = [Sz, Sz @ Sz, Sp + Sm, np.diag(np.arange(1.0, st.d + 1))]
+    ops2 = [np.kron(Sz, Sz) + 0.5 * (np.kron(Sp, Sm) + np.kron(Sm, Sp)), np.kron(Sz, I2), np.kron(I2, Sz),
+            np.kron(Sp, Sm)]
+    for _ in range(args.warmup):
+        e1, e2, _ = eng.local_expectations(ops1, ops2)
+    ms = []
+    for _ in range(args.steps):
+        e1, e2, m_ = eng.local_expectations(ops1, ops2)
+        ms.append(m_)
+    bonds = [eng.icmps_bond(b) for b in range(L + 1)]
+    psi_elems = sum(bonds[j][q] * bonds[j + 1][q + s] for j in range(L) for q in bonds[j] for s in qn
+                    if q + s in bonds[j + 1])
+    theta_elems = sum(bonds[j][q] * bonds[j + 2][q + a + b] for j in range(L - 1) for q in bonds[j] for a in qn
+                      for b in qn if q + a + b in bonds[j + 2])
+    oc_err = 0.0
+    for j in (0, L // 3, L // 2, L - 1):
+        blocks = wl.unpack_site(eng.icmps_site(j), bonds[j], bonds[j + 1], qn)
+        for side in (0, 1):
+            b = j if side == 0 else j + 1
+            off = 0
+            for q, k in bonds[b].items():
+                lam = np.ones(1) if b in (0, L) else 1.0 / eng.icmps_v(b)[off: off + k]
+                off += k
+                if side == 0:
+                    M = sum(x @ x.T for (ql, s), x in blocks.items() if ql == q)
+                else:
+                    M = sum(x.T @ x for (ql, s), x in blocks.items() if ql + qn[s] == q)
+                oc_err = max(oc_err, float(np.abs(M - np.diag(lam ** 2)).max()))
+    out = {"mode": "observe", "workload": f"heisenberg_square_cylinder_{args.lx}x{args.ly}_random_m{args.obs_m}",
+           "sites": L, "max_bond": max(sum(b.values()) for b in bonds), "gauge_s": gauge_s,
+           "measure_ms_median": float(np.median(ms)), "measure_ms_all": ms, "n_ops1": len(ops1),
+           "n_ops2": len(ops2), "psi_slab_MB": psi_elems * 8 / 1e6, "theta_slab_MB": theta_elems * 8 / 1e6,
+           "sz_sum": float(e1[0].sum()), "sz_sum_expected": mpo.qtot / 2, "oc_max_err_sampled": oc_err,
+           "bond_energy_sum": float(e2[0].sum())}
+    eng.close()
     print(json.dumps(out))
 
 
@@ -546,6 +610,9 @@ def main():
         return
     if args.mode == "grad":
         grad_mode(args)
+        return
+    if args.mode == "observe":
+        observe_mode(args)
         return
     if args.mode == "chain":
         chain_mode(args)

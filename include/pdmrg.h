@@ -209,6 +209,43 @@ dmrg_status dmrg_energy_gradient(dmrg_ctx* ctx, double* Wbar, double* E_out);
  * dmrg_set_mps.  Region mode: DMRG_ERR_STATE.  Synchronises the stream. */
 dmrg_status dmrg_get_site(dmrg_ctx* ctx, int j, double* out, long long cap, long long* n_out);
 
+/* Inverse canonical gauge of the serial state (Sec. IV, Figs. 5 and 6): a copy of the state,
+ * kept in the context, in which every site tensor psi_j = Lambda_j Gamma_j Lambda_{j+1} is an
+ * orthogonality centre and every inner bond b (joining sites b-1 and b) carries the diagonal
+ * V_b = Lambda_b^{-1} of inverse Schmidt weights: |Psi> = psi_0 V_1 psi_1 ... V_{L-1} psi_{L-1}.
+ * Built in FP64 (any precision mode) by untruncated SVDs: the centre is moved to site 0, then
+ * Fig. 5's step (SVD, one copy of Lambda into each neighbour, V on the bond) is taken at every
+ * bond left to right; Schmidt values at or below 1e-12 of the largest are dropped so that V is
+ * finite.  The engine's own state is not changed; a later set_mps, sweep, advance, region set-up
+ * or merge discards the copy.  Region mode: DMRG_ERR_STATE.  Synchronises the stream. */
+dmrg_status dmrg_inverse_canonical(dmrg_ctx* ctx);
+
+/* Sectors of bond b (0..L) of the inverse canonical copy (as dmrg_get_bond). */
+dmrg_status dmrg_icmps_bond(dmrg_ctx* ctx, int b, int* q_out, int* m_out, int cap, int* n_out);
+
+/* V_b = 1/Lambda_b of the inverse canonical copy in the sector order of dmrg_icmps_bond
+ * (ascending within each sector; bonds 0 and L: the single value 1). */
+dmrg_status dmrg_icmps_v(dmrg_ctx* ctx, int b, double* v_out, int cap, int* n_out);
+
+/* Site tensor psi_j of the inverse canonical copy (packed layout of dmrg_set_mps for the bonds
+ * of dmrg_icmps_bond), copied to host memory out[cap]; *n_out = element count
+ * (DMRG_ERR_CAPACITY, with *n_out set, if cap is smaller).  Synchronises the stream. */
+dmrg_status dmrg_icmps_site(dmrg_ctx* ctx, int j, double* out, long long cap, long long* n_out);
+
+/* Local expectation values in the inverse canonical gauge (Sec. IV): as every psi_j is an
+ * orthogonality centre, <O_j> = <psi_j|O|psi_j>/<psi_j|psi_j> and a nearest-neighbour operator
+ * needs only Theta_j = psi_j V_{j+1} psi_{j+1}: <O_{j,j+1}> = <Theta_j|O|Theta_j>/<Theta_j|Theta_j>.
+ * Every site and every bond is measured in one pass (a column scaling, one grouped GEMM forming
+ * all Theta_j, one launch of block dot products, a fixed-order reduction, one contraction per
+ * operator set).  ops1: n_ops1 one-site operators [d][d] (row s, column s'); ops2: n_ops2
+ * two-site operators [d*d][d*d] (row index s1*d + s2); both host, real, caller owned.  Only the
+ * matrix elements between basis states of equal total charge contribute (others vanish in a U(1)
+ * eigenstate).  out1 [n_ops1][L] and out2 [n_ops2][L-1] (host, caller owned; nullable when the
+ * count is 0).  ms_out (nullable): device time of the measurement launches in ms.  Needs
+ * dmrg_inverse_canonical first (else DMRG_ERR_STATE).  Synchronises the stream. */
+dmrg_status dmrg_local_expectations(dmrg_ctx* ctx, int n_ops1, const double* ops1, double* out1,
+                                    int n_ops2, const double* ops2, double* out2, float* ms_out);
+
 /* Orthogonality-centre site of the serial state, or of region k in region mode. */
 dmrg_status dmrg_get_center(dmrg_ctx* ctx, int region, int* site_out);
 

@@ -9,6 +9,9 @@ paper (Stoudenmire & White, "Real-Space Parallel Density Matrix Renormalization 
 * ``oracle.accsvd``   -- the Appendix's recursive accurate SVD.
 * ``oracle.regions``  -- real-space parallel DMRG (Sec. II, Eqs. inverse, isvd, merge and
                          Fig. 4's staggered sweep), regions executed one after another.
+* ``oracle.grad``     -- gradients of the projected-Hamiltonian application (reverse mode).
+* ``oracle.icmps``    -- the inverse canonical gauge of Sec. IV (Lambda V Lambda at every bond)
+                         and one-/two-site local expectation values in it.
 * ``oracle.exact``    -- independent references: exact diagonalisation, the transverse-field
                          Ising free-fermion closed form, the AKLT energy.
 

@@ -118,6 +118,11 @@ def lib():
         L.dmrg_get_center.argtypes = [vp, C.c_int, _ip]
         L.dmrg_get_site.argtypes = [vp, C.c_int, _dp, C.c_longlong, C.POINTER(C.c_longlong)]
         L.dmrg_energy_gradient.argtypes = [vp, _dp, _dp]
+        L.dmrg_inverse_canonical.argtypes = [vp]
+        L.dmrg_icmps_bond.argtypes = [vp, C.c_int, _ip, _ip, C.c_int, _ip]
+        L.dmrg_icmps_v.argtypes = [vp, C.c_int, _dp, C.c_int, _ip]
+        L.dmrg_icmps_site.argtypes = [vp, C.c_int, _dp, C.c_longlong, C.POINTER(C.c_longlong)]
+        L.dmrg_local_expectations.argtypes = [vp, C.c_int, _dp, _dp, C.c_int, _dp, _dp, C.POINTER(C.c_float)]
         L.dmrg_destroy.argtypes = [vp]
         L.dmrg_heff_apply.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp, _dp, vp]
         L.dmrg_heff_apply_noalloc.argtypes = [C.POINTER(BondDesc), vp, vp, vp, vp, vp]
@@ -129,7 +134,8 @@ def lib():
         for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
                      "dmrg_profile_read", "dmrg_merge",
                      "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_get_site",
-                     "dmrg_energy_gradient", "dmrg_destroy",
+                     "dmrg_energy_gradient", "dmrg_destroy", "dmrg_inverse_canonical", "dmrg_icmps_bond",
+                     "dmrg_icmps_v", "dmrg_icmps_site", "dmrg_local_expectations",
                      "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_heff_backward", "dmrg_env_left",
                      "dmrg_env_right",
                      "dmrg_svd_split"):
@@ -335,6 +341,47 @@ class Engine:
             out.append(Wb[off: off + k].reshape(sh))
             off += k
         return out, e.value
+
+    def inverse_canonical(self):
+        """Build the inverse canonical copy of the serial state (every site an orthogonality
+        centre, V = 1/Lambda on every bond)."""
+        _check(lib().dmrg_inverse_canonical(self._h), self._h)
+
+    def icmps_bond(self, b):
+        q = np.zeros(8192, np.int32)
+        m = np.zeros(8192, np.int32)
+        n = C.c_int(0)
+        _check(lib().dmrg_icmps_bond(self._h, int(b), _ptr(q, _ip), _ptr(m, _ip), 8192, C.byref(n)), self._h)
+        return {int(a): int(b_) for a, b_ in zip(q[: n.value], m[: n.value])}
+
+    def icmps_v(self, b):
+        v = np.zeros(65536)
+        n = C.c_int(0)
+        _check(lib().dmrg_icmps_v(self._h, int(b), _ptr(v, _dp), 65536, C.byref(n)), self._h)
+        return v[: n.value].copy()
+
+    def icmps_site(self, j):
+        n = C.c_longlong(0)
+        st = lib().dmrg_icmps_site(self._h, int(j), None, 0, C.byref(n))
+        if st not in (0, 4):
+            _check(st, self._h)
+        v = np.zeros(max(1, n.value))
+        _check(lib().dmrg_icmps_site(self._h, int(j), _ptr(v, _dp), v.size, C.byref(n)), self._h)
+        return v[: n.value].copy()
+
+    def local_expectations(self, ops1=(), ops2=()):
+        """(<O_j> [len(ops1), L], <O_{j,j+1}> [len(ops2), L-1], device ms) from the inverse
+        canonical copy; ops1 are [d, d] matrices, ops2 [d*d, d*d] (row index s1*d + s2)."""
+        d = len(self.qn)
+        o1 = _f64(np.asarray(ops1, dtype=np.float64).reshape(-1, d, d))
+        o2 = _f64(np.asarray(ops2, dtype=np.float64).reshape(-1, d * d, d * d))
+        n1, n2 = o1.shape[0], o2.shape[0]
+        e1 = np.zeros((max(1, n1), self.L))
+        e2 = np.zeros((max(1, n2), max(1, self.L - 1)))
+        ms = C.c_float(0.0)
+        _check(lib().dmrg_local_expectations(self._h, n1, _ptr(o1, _dp), _ptr(e1, _dp), n2, _ptr(o2, _dp),
+                                             _ptr(e2, _dp), C.byref(ms)), self._h)
+        return e1[:n1], e2[:n2, : self.L - 1], ms.value
 
     def state(self):
         """(bonds, packed site data, centre) of the serial state, for set_mps."""

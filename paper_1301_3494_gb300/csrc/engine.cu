@@ -104,6 +104,7 @@ struct dmrg_ctx {
     bool have_state = false;
     int dir = 1;                                     // serial sweep direction of dmrg_advance
     std::string last_err;
+    std::unique_ptr<ICMPS, void (*)(ICMPS*)> ic{nullptr, icmps_free};   // inverse canonical copy of the state
 
     const TwoSiteMPO& pair(int j) {
         if (!w12[j]) w12[j].reset(new TwoSiteMPO(two_site_mpo(W[j], W[j + 1])));
@@ -695,6 +696,7 @@ dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_c
 dmrg_status dmrg_set_mps(dmrg_ctx* c, const dmrg_mps_desc* m) {
     CTX_TRY
     PD_REQUIRE(c && m && m->n_sectors && m->sector_q && m->sector_m && m->data, DMRG_ERR_ARG, "null argument");
+    c->ic.reset();
     c->reg.clear();
     c->bounds.clear();
     c->V.clear();
@@ -748,6 +750,7 @@ dmrg_status dmrg_sweep(dmrg_ctx* c, const dmrg_sweep_params* p, dmrg_sweep_stats
     PD_REQUIRE(c && p, DMRG_ERR_ARG, "null argument");
     PD_REQUIRE(c->have_state, DMRG_ERR_STATE, "no state loaded");
     PD_REQUIRE(p->m_max >= 1 && p->dav_max_iter >= 1 && p->dav_tol >= 0, DMRG_ERR_ARG, "bad sweep parameters");
+    c->ic.reset();
     auto t0 = std::chrono::steady_clock::now();
     StepStats tot;
     if (c->reg.empty()) {
@@ -787,6 +790,7 @@ dmrg_status dmrg_advance(dmrg_ctx* c, int n_steps, const dmrg_sweep_params* p, d
     PD_REQUIRE(c && p && n_steps >= 0, DMRG_ERR_ARG, "bad argument");
     PD_REQUIRE(c->have_state && c->reg.empty(), DMRG_ERR_STATE, "advance needs a serial state");
     PD_REQUIRE(p->m_max >= 1 && p->dav_max_iter >= 1 && p->dav_tol >= 0, DMRG_ERR_ARG, "bad sweep parameters");
+    c->ic.reset();
     auto t0 = std::chrono::steady_clock::now();
     Chain& ch = *c->serial;
     ch.acc = StepStats();
@@ -824,6 +828,7 @@ dmrg_status dmrg_setup_regions(dmrg_ctx* c, int n_regions, int warmup, const dmr
     PD_REQUIRE(c->have_state, DMRG_ERR_STATE, "no state loaded");
     PD_REQUIRE(n_regions >= 1 && warmup >= 0, DMRG_ERR_ARG, "bad region count or warm-up");
     PD_REQUIRE(c->reg.empty(), DMRG_ERR_STATE, "regions are already set up");
+    c->ic.reset();
     if (n_regions == 1) return DMRG_OK;
     setup_regions(c, n_regions, warmup, p);
     return DMRG_OK;
@@ -834,6 +839,7 @@ dmrg_status dmrg_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* f
     CTX_TRY
     PD_REQUIRE(c && p, DMRG_ERR_ARG, "null argument");
     PD_REQUIRE(!c->reg.empty() && k >= 1 && k < (int)c->reg.size(), DMRG_ERR_ARG, "no such boundary");
+    c->ic.reset();
     do_merge(c, k, p, fidelity_out, energy_out);
     return DMRG_OK;
     CTX_CATCH(c)
@@ -938,6 +944,68 @@ dmrg_status dmrg_get_site(dmrg_ctx* c, int j, double* out, long long cap, long l
     PD_REQUIRE(S.size <= cap && out, DMRG_ERR_CAPACITY, "capacity too small");
     if (S.size) PD_CK(cudaMemcpyAsync(out, ch.site[j].p, S.size * 8, cudaMemcpyDeviceToHost, ch.st));
     PD_CK(cudaStreamSynchronize(ch.st));
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_inverse_canonical(dmrg_ctx* c) {
+    CTX_TRY
+    PD_REQUIRE(c && c->have_state, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->reg.empty(), DMRG_ERR_STATE, "the inverse canonical gauge is built from a serial state");
+    Chain& ch = *c->serial;
+    std::vector<const double*> sites(c->L);
+    for (int j = 0; j < c->L; ++j) sites[j] = ch.site[j].as<double>();
+    c->ic.reset();
+    c->ic.reset(icmps_build(ch.bond, sites, ch.oc, c->qn, ch.st));
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_icmps_bond(dmrg_ctx* c, int b, int* q, int* m, int cap, int* n) {
+    CTX_TRY
+    PD_REQUIRE(c && n && b >= 0 && b <= c->L, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->ic != nullptr, DMRG_ERR_STATE, "no inverse canonical gauge built");
+    const Sec& s = icmps_bond(*c->ic, b);
+    *n = s.n();
+    PD_REQUIRE(s.n() <= cap && q && m, DMRG_ERR_CAPACITY, "capacity too small");
+    for (int i = 0; i < s.n(); ++i) { q[i] = s.q[i]; m[i] = s.m[i]; }
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_icmps_v(dmrg_ctx* c, int b, double* v, int cap, int* n) {
+    CTX_TRY
+    PD_REQUIRE(c && n && b >= 0 && b <= c->L, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->ic != nullptr, DMRG_ERR_STATE, "no inverse canonical gauge built");
+    const auto& lam = icmps_lambda(*c->ic, b);
+    *n = (int)lam.size();
+    PD_REQUIRE((int)lam.size() <= cap && v, DMRG_ERR_CAPACITY, "capacity too small");
+    for (size_t i = 0; i < lam.size(); ++i) v[i] = 1.0 / lam[i];
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_icmps_site(dmrg_ctx* c, int j, double* out, long long cap, long long* n) {
+    CTX_TRY
+    PD_REQUIRE(c && n && j >= 0 && j < c->L, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE(c->ic != nullptr, DMRG_ERR_STATE, "no inverse canonical gauge built");
+    const long long sz = icmps_site_size(*c->ic, j);
+    *n = sz;
+    PD_REQUIRE(sz <= cap && out, DMRG_ERR_CAPACITY, "capacity too small");
+    cudaStream_t st = c->serial->st;
+    if (sz) PD_CK(cudaMemcpyAsync(out, icmps_site_dev(*c->ic, j), sz * 8, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    return DMRG_OK;
+    CTX_CATCH(c)
+}
+
+dmrg_status dmrg_local_expectations(dmrg_ctx* c, int n_ops1, const double* ops1, double* out1, int n_ops2,
+                                    const double* ops2, double* out2, float* ms_out) {
+    CTX_TRY
+    PD_REQUIRE(c && n_ops1 >= 0 && n_ops2 >= 0, DMRG_ERR_ARG, "bad argument");
+    PD_REQUIRE((n_ops1 == 0 || (ops1 && out1)) && (n_ops2 == 0 || (ops2 && out2)), DMRG_ERR_ARG, "null operator or output");
+    PD_REQUIRE(c->ic != nullptr, DMRG_ERR_STATE, "no inverse canonical gauge built");
+    icmps_expectations(*c->ic, c->qn, n_ops1, ops1, out1, n_ops2, ops2, out2, ms_out, c->serial->st);
     return DMRG_OK;
     CTX_CATCH(c)
 }

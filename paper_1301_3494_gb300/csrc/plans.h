@@ -341,6 +341,23 @@ struct DavResult {
 DavResult davidson(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, double* x, int kmax, double tol,
                    int max_iter, unsigned* err, cudaStream_t st, HeffPlan* acc = nullptr, int refine_iters = 0);
 
+// Inverse canonical MPS gauge (Sec. IV): psi_j = Lambda_j Gamma_j Lambda_{j+1} on every site,
+// V_b = Lambda_b^-1 on every inner bond, all site tensors in one FP64 slab.  Built from packed
+// site tensors (bonds[0..L]) of a mixed-canonical state with its centre at `oc`; synchronises.
+struct ICMPS;
+ICMPS* icmps_build(const std::vector<Sec>& bonds, const std::vector<const double*>& sites, int oc,
+                   const std::vector<int>& qn, cudaStream_t st);
+void icmps_free(ICMPS* p);
+const Sec& icmps_bond(const ICMPS& ic, int b);
+const std::vector<double>& icmps_lambda(const ICMPS& ic, int b);
+long long icmps_site_size(const ICMPS& ic, int j);
+const double* icmps_site_dev(const ICMPS& ic, int j);
+// One- and two-site expectation values over every site and every nearest-neighbour bond:
+// ops1 [n1][d][d], ops2 [n2][d*d][d*d] (host, row index s1*d + s2), out1 [n1][L], out2 [n2][L-1]
+// (host).  ms_out (nullable): device time of the measurement launches.  Synchronises.
+void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, const double* ops1, double* out1, int n2,
+                        const double* ops2, double* out2, float* ms_out, cudaStream_t st);
+
 // Scale the blocks of a packed site tensor (bonds bl x br) by a per-sector vector `lam` of
 // the right bond (right_index = true: out[a][t] = in[a][t] lam[t]) or of the left bond
 // (right_index = false: out[t][c] = lam[t] in[t][c]).
