@@ -97,6 +97,11 @@ typedef struct {
     void* stream;           /* cudaStream_t base stream (region streams are forked from it)   */
     int svd_fp64;           /* mixed modes: 1 = ordinary-bond splits in FP64 as well (slower;
                                0 = FP32 block Jacobi + FP64 re-orthonormalisation)             */
+    int fp64_emulation;     /* 1 = the context's FP64 grouped GEMMs (FP64-mode matvec and
+                               environment updates, wavefunction formation, gauge moves, local
+                               measurements) run FP64-accurate on the bf16 tensor cores
+                               (dmrg_gemm64 mode 1); batches outside its K limit stay on the
+                               FP64 units.  0 = FP64 units throughout.                          */
 } dmrg_config;
 
 typedef struct {
@@ -376,6 +381,39 @@ dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int 
                            int accurate, double* A_dev, double* lam_dev, double* B_dev,
                            int cap, int* nm_out, int* qm_out, int* mm_out, double* trunc_out,
                            void* stream);
+
+/* One problem of a grouped FP64 GEMM:
+ *   C(m, n) (+)= alpha * sum over its segments sum_{k < K} A(m, k) B(n, k),   m < M, n < N,
+ *   A(m, k) = A[a_off + m*sam + k*sak], B(n, k) = B[b_off + n*sbn + k*sbk],
+ *   C(m, n) = C[c_off + m*scm + n*scn];  accumulate = 0: C = ..., 1: C += ...
+ * Segments seg0 .. seg0 + nseg - 1 of the segment array.  No two problems of one call may
+ * write the same element of C.  (The block contractions of Sec. II -- projected Hamiltonian,
+ * operator transformation, two-site wavefunction -- are all batches of this form.) */
+typedef struct {
+    int M, N, seg0, nseg;
+    long long c_off;
+    int sam, sak, sbn, sbk, scm, scn;
+    int accumulate, pad_;
+    double alpha;
+} dmrg_gemm_problem;
+typedef struct {
+    long long a_off, b_off;
+    int K, pad_;
+} dmrg_gemm_segment;
+
+/* Grouped FP64 GEMM on device buffers A_dev, B_dev, C_dev (caller owned; every addressed
+ * element must lie inside them -- not checked).  mode 0: the FP64 units.  mode 1: FP64-accurate
+ * emulation on the bf16 tensor cores (Ozaki, Ogita and Oishi's error-free splitting): each
+ * operand row is scaled by a power of two and cut into s slices of beta bits, the slice
+ * products are summed exactly in FP32 on the tensor cores and combined in FP64; the error is
+ * below (s^2/2 + 2) 2^(-s beta) max_k|A(m,k)| max_k|B(n,k)| per term (s beta >= 56), at the level
+ * of FP64 rounding.  info (nullable, int[3]): beta, s and the number of FP32 accumulators per
+ * problem (0, 0, 0 in mode 0).  Errors: DMRG_ERR_ARG (bad problem or segment), DMRG_ERR_STATE
+ * (mode 1 without sm_103 tensor cores), DMRG_ERR_CAPACITY (mode 1 with a K too large for exact
+ * FP32 accumulation, about 2 million per problem).  Synchronises the stream. */
+dmrg_status dmrg_gemm64(const dmrg_gemm_problem* probs, int n_probs, const dmrg_gemm_segment* segs, int n_segs,
+                        const double* A_dev, const double* B_dev, double* C_dev, int mode, int* info,
+                        void* stream);
 
 #ifdef __cplusplus
 }

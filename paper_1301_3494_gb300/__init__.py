@@ -52,7 +52,8 @@ class Profile(C.Structure):
 
 
 class Config(C.Structure):
-    _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p), ("svd_fp64", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p), ("svd_fp64", C.c_int),
+                ("fp64_emulation", C.c_int)]
 
 
 class SweepParams(C.Structure):
@@ -69,6 +70,16 @@ class SweepStats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GemmProblem(C.Structure):
+    _fields_ = [("M", C.c_int), ("N", C.c_int), ("seg0", C.c_int), ("nseg", C.c_int), ("c_off", C.c_longlong),
+                ("sam", C.c_int), ("sak", C.c_int), ("sbn", C.c_int), ("sbk", C.c_int), ("scm", C.c_int),
+                ("scn", C.c_int), ("accumulate", C.c_int), ("pad_", C.c_int), ("alpha", C.c_double)]
+
+
+class GemmSegment(C.Structure):
+    _fields_ = [("a_off", C.c_longlong), ("b_off", C.c_longlong), ("K", C.c_int), ("pad_", C.c_int)]
 
 
 class BondDesc(C.Structure):
@@ -129,6 +140,8 @@ def lib():
         L.dmrg_heff_backward.argtypes = [C.POINTER(BondDesc), vp, vp, vp, vp, vp, vp, vp, _dp, _dp, vp]
         L.dmrg_env_left.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
         L.dmrg_env_right.argtypes = [C.POINTER(BondDesc), C.c_int, vp, vp, vp, vp]
+        L.dmrg_gemm64.argtypes = [C.POINTER(GemmProblem), C.c_int, C.POINTER(GemmSegment), C.c_int, vp, vp, vp, C.c_int,
+                                  _ip, vp]
         L.dmrg_svd_split.argtypes = [C.POINTER(BondDesc), vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, _ip, _ip, _ip,
                                      _dp, vp]
         for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
@@ -138,7 +151,7 @@ def lib():
                      "dmrg_icmps_v", "dmrg_icmps_site", "dmrg_local_expectations",
                      "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_heff_backward", "dmrg_env_left",
                      "dmrg_env_right",
-                     "dmrg_svd_split"):
+                     "dmrg_svd_split", "dmrg_gemm64"):
             getattr(L, name).restype = st
         _lib = L
     return _lib
@@ -244,13 +257,31 @@ def svd_split(bond: Bond, psi_dev, m_max, accurate, A_dev, lam_dev, B_dev, cap=4
     return {int(q): int(m) for q, m in zip(qm[: nm.value], mm[: nm.value])}, tr.value
 
 
+def gemm64(problems, segments, A_dev, B_dev, C_dev, mode=0, stream=0):
+    """Grouped FP64 GEMM (dmrg_gemm64).  problems: tuples (M, N, seg0, nseg, c_off, sam, sak, sbn,
+    sbk, scm, scn, accumulate, alpha); segments: tuples (a_off, b_off, K).  mode 0: FP64 units,
+    1: FP64-accurate emulation on the bf16 tensor cores.  Returns (beta, s, accumulators)."""
+    P = (GemmProblem * max(1, len(problems)))()
+    for i, t in enumerate(problems):
+        M, N, seg0, nseg, c_off, sam, sak, sbn, sbk, scm, scn, acc, alpha = t
+        P[i] = GemmProblem(M, N, seg0, nseg, c_off, sam, sak, sbn, sbk, scm, scn, acc, 0, alpha)
+    S = (GemmSegment * max(1, len(segments)))()
+    for i, (a, b, k) in enumerate(segments):
+        S[i] = GemmSegment(a, b, k, 0)
+    info = np.zeros(3, np.int32)
+    _check(lib().dmrg_gemm64(P, len(problems), S, len(segments), C.c_void_p(A_dev), C.c_void_p(B_dev),
+                             C.c_void_p(C_dev), int(mode), _ptr(info, _ip), C.c_void_p(stream)))
+    return tuple(int(x) for x in info)
+
+
 # ------------------------------------------------------------------------------------------
 # Context-level engine
 # ------------------------------------------------------------------------------------------
 class Engine:
     """A DMRG state on the GPU: MPO, MPS, environments, optional real-space regions."""
 
-    def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0, svd_fp64=False):
+    def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0, svd_fp64=False,
+                 fp64_emulation=False):
         self._keep = [_f64(W), _i32(flux), _i32(D), _i32(qn)]
         W_, f_, D_, q_ = self._keep
         self.L = len(D_) - 1
@@ -258,7 +289,7 @@ class Engine:
         self._wshapes = [(int(D_[j]), len(q_), len(q_), int(D_[j + 1])) for j in range(self.L)]
         desc = MpoDesc(self.L, len(q_), _ptr(q_, _ip), _ptr(D_, _ip), _ptr(f_, _ip), _ptr(W_, _dp), int(qtot))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)))
+        cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)), int(bool(fp64_emulation)))
         h = C.c_void_p()
         _check(lib().dmrg_init_mpo(C.byref(h), C.byref(desc), C.byref(cfg)))
         self._h = h

@@ -194,4 +194,48 @@ dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int 
     }
 }
 
+dmrg_status dmrg_gemm64(const dmrg_gemm_problem* probs, int n_probs, const dmrg_gemm_segment* segs, int n_segs,
+                        const double* A_dev, const double* B_dev, double* C_dev, int mode, int* info, void* stream) {
+    try {
+        PD_REQUIRE(n_probs >= 0 && n_segs >= 0 && (n_probs == 0 || (probs && segs)), DMRG_ERR_ARG, "bad problem list");
+        PD_REQUIRE(mode == 0 || mode == 1, DMRG_ERR_ARG, "mode must be 0 or 1");
+        PD_REQUIRE(A_dev && B_dev && C_dev, DMRG_ERR_ARG, "null buffer");
+        cudaStream_t st = (cudaStream_t)stream;
+        GemmBatch g;
+        for (int i = 0; i < n_probs; ++i) {
+            const dmrg_gemm_problem& p = probs[i];
+            PD_REQUIRE(p.M >= 0 && p.N >= 0 && p.nseg >= 1 && p.seg0 >= 0 && p.seg0 + p.nseg <= n_segs, DMRG_ERR_ARG,
+                       "bad problem");
+            std::vector<GSeg> sg;
+            for (int k = 0; k < p.nseg; ++k) {
+                const dmrg_gemm_segment& s = segs[p.seg0 + k];
+                PD_REQUIRE(s.K >= 1, DMRG_ERR_ARG, "segment K must be >= 1");
+                sg.push_back({s.a_off, s.b_off, s.K, 0});
+            }
+            g.add(p.M, p.N, p.c_off, p.sam, p.sak, p.sbn, p.sbk, p.scm, p.scn, sg, p.accumulate ? 1 : 0, p.alpha);
+        }
+        if (info) info[0] = info[1] = info[2] = 0;
+        if (mode == 1) {
+            PD_REQUIRE(tc_available(), DMRG_ERR_STATE, "FP64 emulation needs sm_103 tensor cores");
+            PD_REQUIRE(run_gemm64_emu(g, A_dev, B_dev, C_dev, st), DMRG_ERR_CAPACITY,
+                       "K too large for exact FP32 accumulation");
+            if (info) emu_plan_info(g, info, info + 1, info + 2);
+        } else {
+            const int saved = g_gemm64_emu;
+            g_gemm64_emu = 0;
+            try {
+                run_gemm64(g, A_dev, B_dev, C_dev, st);
+            } catch (...) {
+                g_gemm64_emu = saved;
+                throw;
+            }
+            g_gemm64_emu = saved;
+        }
+        PD_CK(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    }
+}
+
 }  // extern "C"

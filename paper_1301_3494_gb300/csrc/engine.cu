@@ -95,6 +95,7 @@ struct dmrg_ctx {
     std::vector<std::unique_ptr<TwoSiteMPO>> w12;   // per bond (j, j+1), lazily built
     int prec = DMRG_FP64, kmax = 8;
     bool svd_fp64 = false;       // mixed modes: FP64 splits on ordinary bonds too
+    bool emu = false;            // FP64 grouped GEMMs on the bf16 tensor cores (ozaki.cu)
     cudaStream_t base = nullptr;
     std::unique_ptr<Chain> serial;
     std::vector<std::unique_ptr<Chain>> reg;
@@ -350,11 +351,13 @@ void parallel_items(const std::vector<int>& items, F fn, bool serial = false) {
     PD_CK(cudaGetDevice(&dev));
     PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int cap = items.size() > 1 ? std::max(1, sms / (int)items.size()) : 0;
+    const int emu = g_gemm64_emu;
     for (size_t t = 0; t < items.size(); ++t)
         th.emplace_back([&, t]() {
             try {
                 PD_CK(cudaSetDevice(dev));
                 g_sm_cap = cap;
+                g_gemm64_emu = emu;
                 fn(items[t]);
             } catch (const Error& e) {
                 errs[t] = e;
@@ -620,7 +623,13 @@ StepStats region_sweep(dmrg_ctx* c, const dmrg_sweep_params* p) {
 // ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------
-#define CTX_TRY try {
+// The context's FP64-GEMM choice holds on the calling thread for the duration of the call.
+struct EmuGuard {
+    int saved;
+    explicit EmuGuard(const dmrg_ctx* c) : saved(g_gemm64_emu) { g_gemm64_emu = (c && c->emu) ? 1 : 0; }
+    ~EmuGuard() { g_gemm64_emu = saved; }
+};
+#define CTX_TRY try { EmuGuard emu_guard_(c);
 #define CTX_CATCH(ctx)                                        \
     }                                                         \
     catch (const Error& e) {                                  \
@@ -676,6 +685,8 @@ dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_c
     C->prec = cfg->precision;
     C->kmax = cfg->kmax > 0 ? cfg->kmax : 8;
     C->svd_fp64 = cfg->svd_fp64 != 0;
+    C->emu = cfg->fp64_emulation != 0;
+    PD_REQUIRE(!C->emu || tc_available(), DMRG_ERR_STATE, "FP64 emulation needs sm_103 tensor cores");
     PD_REQUIRE(C->kmax >= 2 && C->kmax <= 32, DMRG_ERR_ARG, "kmax must be in [2, 32]");
     C->base = (cudaStream_t)cfg->stream;
     PD_REQUIRE(mpo->D[0] == 1 && mpo->D[C->L] == 1, DMRG_ERR_ARG, "D[0] and D[L] must be 1");

@@ -24,16 +24,7 @@
 #include "plans.h"
 
 namespace pd {
-
-struct ICMPS {
-    int L = 0;
-    std::vector<Sec> bond;                    // L + 1
-    std::vector<long long> site_off;          // L + 1, offsets into psi
-    std::vector<long long> v_off;             // L + 1, offsets into V (bonds 1..L-1 used)
-    std::vector<std::vector<double>> lam;     // L + 1 (host copies, sector order)
-    DBuf psi, V;
-};
-
+struct ICMPS;
 }  // namespace pd
 
 using namespace pd;
@@ -155,6 +146,29 @@ void absorb(const Sec& carry_l, const Sec& carry_r, const Sec& site_l, const Sec
 
 namespace pd {
 
+// Host lists and device buffers of one measurement pass over a gauge (they depend only on its
+// block structure and on which operator sets are measured), kept for later passes.
+struct MeasPlan {
+    bool with1 = false, with2 = false;
+    std::vector<IcScale> scale;
+    GemmBatch theta;
+    std::vector<IcDot> dots;
+    std::vector<int> t0, gidx;
+    long long g_size = 0, g2_base = 0, p_size = 0, th_size = 0;
+    DBuf dscale, ddots, dt0, dg, part, G, P, Th, o1, o2, dops1, dops2;
+};
+
+struct ICMPS {
+    int L = 0;
+    std::vector<Sec> bond;                    // L + 1
+    std::vector<long long> site_off;          // L + 1, offsets into psi
+    std::vector<long long> v_off;             // L + 1, offsets into V (bonds 1..L-1 used)
+    std::vector<std::vector<double>> lam;     // L + 1 (host copies, sector order)
+    DBuf psi, V;
+    std::unique_ptr<MeasPlan> plan;           // last measurement plan
+};
+
+
 void icmps_free(ICMPS* p) { delete p; }
 
 ICMPS* icmps_build(const std::vector<Sec>& bonds, const std::vector<const double*>& sites, int oc,
@@ -235,18 +249,19 @@ const std::vector<double>& icmps_lambda(const ICMPS& ic, int b) { return ic.lam.
 long long icmps_site_size(const ICMPS& ic, int j) { return ic.site_off.at(j + 1) - ic.site_off.at(j); }
 const double* icmps_site_dev(const ICMPS& ic, int j) { return ic.psi.as<double>() + ic.site_off.at(j); }
 
-// ops1: [n1][d][d], ops2: [n2][d*d][d*d] (host); out1: [n1][L], out2: [n2][L-1] (host).
-void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, const double* ops1, double* out1, int n2,
-                        const double* ops2, double* out2, float* ms_out, cudaStream_t st) {
+static std::unique_ptr<MeasPlan> make_meas_plan(const ICMPS& ic, const std::vector<int>& qn, bool with1, bool with2,
+                                         cudaStream_t st) {
     const int L = ic.L, d = (int)qn.size(), D2 = d * d;
-    // ---- host plans ----
+    std::unique_ptr<MeasPlan> M(new MeasPlan());
+    M->with1 = with1;
+    M->with2 = with2;
     std::vector<SiteLayout> S(L);
     for (int j = 0; j < L; ++j) S[j] = site_layout(ic.bond[j], ic.bond[j + 1], qn);
     struct Pair { long long a, b, len; };
     std::map<long long, std::vector<Pair>> gram;            // Gram element -> equally shaped block pairs
-    const long long g2_base = (long long)L * d * d;
-    const long long g_size = g2_base + (long long)std::max(0, L - 1) * D2 * D2;
-    if (n1 > 0)
+    M->g2_base = (long long)L * d * d;
+    M->g_size = M->g2_base + (long long)std::max(0, L - 1) * D2 * D2;
+    if (with1)
         for (int j = 0; j < L; ++j)
             for (int i = 0; i < ic.bond[j].n(); ++i)
                 for (int s = 0; s < d; ++s)
@@ -259,10 +274,8 @@ void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, con
                             {ic.site_off[j] + bx.off, ic.site_off[j] + S[j].blk[y].off, (long long)bx.rows * bx.cols});
                     }
     // bonds: P_j = psi_j V_{j+1} (column scaling), Theta_j = P_j psi_{j+1}
-    std::vector<IcScale> scale;
-    GemmBatch g;
     std::vector<long long> th_off(std::max(1, L), 0);
-    if (n2 > 0) {
+    if (with2) {
         for (int j = 0; j + 1 < L; ++j) {
             const Sec& bm = ic.bond[j + 1];
             std::vector<long long> moff(bm.n() + 1, 0);
@@ -270,8 +283,8 @@ void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, con
             for (const auto& bk : S[j].blk) {
                 const long long n = (long long)bk.rows * bk.cols;
                 for (long long e0 = 0; e0 < n; e0 += kDotChunk)
-                    scale.push_back({ic.site_off[j] + bk.off, ic.v_off[j + 1] + moff[bk.j], (int)e0,
-                                     (int)std::min<long long>(kDotChunk, n - e0), bk.cols, 0});
+                    M->scale.push_back({ic.site_off[j] + bk.off, ic.v_off[j + 1] + moff[bk.j], (int)e0,
+                                        (int)std::min<long long>(kDotChunk, n - e0), bk.cols, 0});
             }
             const PsiLayout P = psi_layout(ic.bond[j], ic.bond[j + 2], qn);
             for (const auto& b : P.blk) {
@@ -280,8 +293,9 @@ void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, con
                 const int lb = S[j].at(b.i, b.s1), rb = S[j + 1].at(im, b.s2);
                 if (lb < 0 || rb < 0) continue;
                 // C(m = c, n = a) = sum_mid psi_{j+1}[mid][c] P_j[a][mid]
-                g.add(b.cols, b.rows, th_off[j] + b.off, 1, b.cols, bm.m[im], 1, 1, b.cols,
-                      {GSeg{ic.site_off[j + 1] + S[j + 1].blk[rb].off, ic.site_off[j] + S[j].blk[lb].off, bm.m[im], 0}});
+                M->theta.add(b.cols, b.rows, th_off[j] + b.off, 1, b.cols, bm.m[im], 1, 1, b.cols,
+                             {GSeg{ic.site_off[j + 1] + S[j + 1].blk[rb].off, ic.site_off[j] + S[j].blk[lb].off,
+                                   bm.m[im], 0}});
             }
             for (int i = 0; i < ic.bond[j].n(); ++i)
                 for (int p = 0; p < D2; ++p)
@@ -291,81 +305,91 @@ void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, con
                         const int x = P.at(i, s1, s2), y = P.at(i, t1, t2);
                         if (x < 0 || y < 0) continue;
                         const auto& bx = P.blk[x];
-                        gram[g2_base + ((long long)j * D2 + p) * D2 + pp].push_back(
+                        gram[M->g2_base + ((long long)j * D2 + p) * D2 + pp].push_back(
                             {-1 - (th_off[j] + bx.off), th_off[j] + P.blk[y].off, (long long)bx.rows * bx.cols});
                     }
             th_off[j + 1] = th_off[j] + P.size;
         }
     }
     // flatten: one reduce entry per Gram element, its chunks contiguous in the listed order
-    std::vector<IcDot> dots;
-    std::vector<int> t0, gidx;
     for (const auto& kv : gram) {
-        t0.push_back((int)dots.size());
-        gidx.push_back((int)kv.first);
+        M->t0.push_back((int)M->dots.size());
+        M->gidx.push_back((int)kv.first);
         for (const auto& pr : kv.second) {
             const int slab = pr.a < 0 ? 1 : 0;
             const long long a = pr.a < 0 ? -1 - pr.a : pr.a;
             for (long long c = 0; c < pr.len; c += kDotChunk)
-                dots.push_back({a + c, pr.b + c, (int)std::min<long long>(kDotChunk, pr.len - c), slab});
+                M->dots.push_back({a + c, pr.b + c, (int)std::min<long long>(kDotChunk, pr.len - c), slab});
         }
     }
-    t0.push_back((int)dots.size());
-    PD_REQUIRE(dots.size() < (size_t)INT32_MAX && scale.size() < (size_t)INT32_MAX && g_size < (long long)INT32_MAX, DMRG_ERR_CAPACITY,
-               "too many blocks to measure at once");
-    DBuf dscale, ddots, dt0, dg, dops1, dops2, part, G, P, Th, o1, o2;
-    upload(dscale, scale, st);
-    upload(ddots, dots, st);
-    upload(dt0, t0, st);
-    upload(dg, gidx, st);
-    if (n1 > 0) upload(dops1, std::vector<double>(ops1, ops1 + (size_t)n1 * d * d), st);
-    if (n2 > 0) upload(dops2, std::vector<double>(ops2, ops2 + (size_t)n2 * D2 * D2), st);
-    part.ensure(std::max<size_t>(1, dots.size()) * 8, st);
-    G.ensure(std::max<long long>(1, g_size) * 8, st);
-    const long long p_size = L > 1 ? ic.site_off[L - 1] : 0;
-    const long long th_size = L > 1 ? th_off[L - 1] : 0;
-    if (n2 > 0) {
-        P.ensure(std::max<long long>(1, p_size) * 8, st);
-        Th.ensure(std::max<long long>(1, th_size) * 8, st);
+    M->t0.push_back((int)M->dots.size());
+    PD_REQUIRE(M->dots.size() < (size_t)INT32_MAX && M->scale.size() < (size_t)INT32_MAX &&
+                   M->g_size < (long long)INT32_MAX,
+               DMRG_ERR_CAPACITY, "too many blocks to measure at once");
+    upload(M->dscale, M->scale, st);
+    upload(M->ddots, M->dots, st);
+    upload(M->dt0, M->t0, st);
+    upload(M->dg, M->gidx, st);
+    M->part.ensure(std::max<size_t>(1, M->dots.size()) * 8, st);
+    M->G.ensure(std::max<long long>(1, M->g_size) * 8, st);
+    M->p_size = L > 1 ? ic.site_off[L - 1] : 0;
+    M->th_size = L > 1 ? th_off[L - 1] : 0;
+    if (with2) {
+        M->P.ensure(std::max<long long>(1, M->p_size) * 8, st);
+        M->Th.ensure(std::max<long long>(1, M->th_size) * 8, st);
+        M->theta.upload_tiles(64, 64, st);
     }
-    o1.ensure(std::max(1, n1 * L) * 8, st);
-    o2.ensure(std::max(1, n2 * std::max(1, L - 1)) * 8, st);
-    if (n2 > 0) g.upload_tiles(64, 64, st);
+    return M;
+}
+
+// ops1: [n1][d][d], ops2: [n2][d*d][d*d] (host); out1: [n1][L], out2: [n2][L-1] (host).
+void icmps_expectations(ICMPS& ic, const std::vector<int>& qn, int n1, const double* ops1, double* out1, int n2,
+                        const double* ops2, double* out2, float* ms_out, cudaStream_t st) {
+    const int L = ic.L, d = (int)qn.size(), D2 = d * d;
+    if (!ic.plan || ic.plan->with1 != (n1 > 0) || ic.plan->with2 != (n2 > 0))
+        ic.plan = make_meas_plan(ic, qn, n1 > 0, n2 > 0, st);
+    MeasPlan& M = *ic.plan;
+    if (n1 > 0) upload(M.dops1, std::vector<double>(ops1, ops1 + (size_t)n1 * d * d), st);
+    if (n2 > 0) upload(M.dops2, std::vector<double>(ops2, ops2 + (size_t)n2 * D2 * D2), st);
+    M.o1.ensure(std::max(1, n1 * L) * 8, st);
+    M.o2.ensure(std::max(1, n2 * std::max(1, L - 1)) * 8, st);
     PD_CK(cudaStreamSynchronize(st));
     // ---- device work ----
     cudaEvent_t e0, e1;
     PD_CK(cudaEventCreate(&e0));
     PD_CK(cudaEventCreate(&e1));
     PD_CK(cudaEventRecord(e0, st));
-    PD_CK(cudaMemsetAsync(G.p, 0, std::max<long long>(1, g_size) * 8, st));
-    if (n2 > 0 && !scale.empty()) {
-        k_ic_colscale<<<(unsigned)scale.size(), 256, 0, st>>>(
-            dscale.as<IcScale>(), ic.psi.as<double>(), ic.V.as<double>(), P.as<double>());
+    PD_CK(cudaMemsetAsync(M.G.p, 0, std::max<long long>(1, M.g_size) * 8, st));
+    if (n2 > 0 && !M.scale.empty()) {
+        k_ic_colscale<<<(unsigned)M.scale.size(), 256, 0, st>>>(M.dscale.as<IcScale>(), ic.psi.as<double>(),
+                                                               ic.V.as<double>(), M.P.as<double>());
         PD_LAUNCHED();
-        PD_CK(cudaMemsetAsync(Th.p, 0, std::max<long long>(1, th_size) * 8, st));
-        run_gemm64(g, ic.psi.as<double>(), P.as<double>(), Th.as<double>(), st);
+        PD_CK(cudaMemsetAsync(M.Th.p, 0, std::max<long long>(1, M.th_size) * 8, st));
+        run_gemm64(M.theta, ic.psi.as<double>(), M.P.as<double>(), M.Th.as<double>(), st);
     }
-    if (!dots.empty()) {
-        k_ic_dot<<<(unsigned)dots.size(), 256, 0, st>>>(ddots.as<IcDot>(), ic.psi.as<double>(), Th.as<double>(),
-                                                        part.as<double>());
+    if (!M.dots.empty()) {
+        k_ic_dot<<<(unsigned)M.dots.size(), 256, 0, st>>>(M.ddots.as<IcDot>(), ic.psi.as<double>(),
+                                                          M.Th.as<double>(), M.part.as<double>());
         PD_LAUNCHED();
-        const int ne = (int)gidx.size();
-        k_ic_reduce<<<gridn(ne, 256), 256, 0, st>>>(dt0.as<int>(), dg.as<int>(), part.as<double>(), ne, G.as<double>());
+        const int ne = (int)M.gidx.size();
+        k_ic_reduce<<<gridn(ne, 256), 256, 0, st>>>(M.dt0.as<int>(), M.dg.as<int>(), M.part.as<double>(), ne,
+                                                    M.G.as<double>());
         PD_LAUNCHED();
     }
     if (n1 > 0) {
-        k_ic_contract<<<gridn((long long)n1 * L, 128), 128, 0, st>>>(G.as<double>(), dops1.as<double>(), n1, L, d,
-                                                                   o1.as<double>());
+        k_ic_contract<<<gridn((long long)n1 * L, 128), 128, 0, st>>>(M.G.as<double>(), M.dops1.as<double>(), n1, L, d,
+                                                                   M.o1.as<double>());
         PD_LAUNCHED();
     }
     if (n2 > 0 && L > 1) {
-        k_ic_contract<<<gridn((long long)n2 * (L - 1), 128), 128, 0, st>>>(G.as<double>() + g2_base, dops2.as<double>(),
-                                                                         n2, L - 1, D2, o2.as<double>());
+        k_ic_contract<<<gridn((long long)n2 * (L - 1), 128), 128, 0, st>>>(M.G.as<double>() + M.g2_base,
+                                                                         M.dops2.as<double>(), n2, L - 1, D2,
+                                                                         M.o2.as<double>());
         PD_LAUNCHED();
     }
     PD_CK(cudaEventRecord(e1, st));
-    if (n1 > 0) PD_CK(cudaMemcpyAsync(out1, o1.p, (size_t)n1 * L * 8, cudaMemcpyDeviceToHost, st));
-    if (n2 > 0 && L > 1) PD_CK(cudaMemcpyAsync(out2, o2.p, (size_t)n2 * (L - 1) * 8, cudaMemcpyDeviceToHost, st));
+    if (n1 > 0) PD_CK(cudaMemcpyAsync(out1, M.o1.p, (size_t)n1 * L * 8, cudaMemcpyDeviceToHost, st));
+    if (n2 > 0 && L > 1) PD_CK(cudaMemcpyAsync(out2, M.o2.p, (size_t)n2 * (L - 1) * 8, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
     float ms = 0.0f;
     PD_CK(cudaEventElapsedTime(&ms, e0, e1));

@@ -43,7 +43,7 @@ extern std::atomic<long long> g_launches;
 
 // Profiling classes of grouped-GEMM launches; the class of tensor-core launches comes from the
 // calling thread's current activity.
-enum ProfClass { PROF_MV = 0, PROF_ENV = 1, PROF_F64 = 2, PROF_F32 = 3 };
+enum ProfClass { PROF_MV = 0, PROF_ENV = 1, PROF_F64 = 2, PROF_F32 = 3, PROF_NONE = 4 };   // NONE: not tallied
 extern thread_local int g_prof_class;
 bool prof_on();
 // With profiling on: record an event pair around a launch (call prof_start before the launch,

@@ -126,6 +126,7 @@ void GemmBatch::upload_tiles(int tm, int tn, cudaStream_t st) {
 
 void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st) {
     if (g.empty()) return;
+    if (g_gemm64_emu && run_gemm64_emu(g, A, B, C, st)) return;
     g.upload_tiles(64, 64, st);
     void* tok = prof_on() ? prof_start(st) : nullptr;
     launch_gemm_simt<double>(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);

@@ -143,6 +143,9 @@ inline Num env_num(int prec) { return prec == DMRG_FP64 ? Num::F64 : Num::F32; }
 // ------------------------------------------------------------------------------------------
 // Grouped GEMM batch (host list -> device arrays -> FP64 SIMT or tcgen05 launch)
 // ------------------------------------------------------------------------------------------
+struct EmuPlan;
+// FP64 GEMMs through the bf16 tensor cores (ozaki.cu) when set on the calling thread.
+extern thread_local int g_gemm64_emu;
 struct GemmBatch {
     std::vector<GProb> probs;
     std::vector<GSeg> segs;
@@ -153,6 +156,7 @@ struct GemmBatch {
     int tile_m = 0, tile_n = 0;
     long long a_rows = 0, b_rows = 0;   // slab extents (tensor-core path)
     int lda = 0, ldb = 0;
+    std::shared_ptr<EmuPlan> emu;       // plan of the FP64-emulated execution, built on first use
 
     void add(int M, int N, long long c_off, int sam, int sak, int sbn, int sbk, int scm, int scn,
              const std::vector<GSeg>& sg, int accumulate = 0, double alpha = 1.0) {
@@ -179,6 +183,12 @@ void run_gemm32(GemmBatch& g, const float* A, const float* B, float* C, cudaStre
 void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B,
                  long long b_rows, int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st);
 bool tc_available();
+// FP64-accurate execution of an FP64 batch on the bf16 tensor cores (error-free slicing, exact
+// FP32 accumulation, FP64 recombination).  Returns false, doing nothing, when the tensor cores
+// are unavailable or the batch's K is too large for exact accumulation.  Synchronises (checks
+// the tensor-core kernel's error word).
+bool run_gemm64_emu(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st);
+void emu_plan_info(const GemmBatch& g, int* beta, int* s, int* groups);
 
 // ------------------------------------------------------------------------------------------
 // Generic job lists uploaded once, launched many times
@@ -354,8 +364,9 @@ long long icmps_site_size(const ICMPS& ic, int j);
 const double* icmps_site_dev(const ICMPS& ic, int j);
 // One- and two-site expectation values over every site and every nearest-neighbour bond:
 // ops1 [n1][d][d], ops2 [n2][d*d][d*d] (host, row index s1*d + s2), out1 [n1][L], out2 [n2][L-1]
-// (host).  ms_out (nullable): device time of the measurement launches.  Synchronises.
-void icmps_expectations(const ICMPS& ic, const std::vector<int>& qn, int n1, const double* ops1, double* out1, int n2,
+// (host).  ms_out (nullable): device time of the measurement launches.  The host lists and
+// buffers of a pass are kept in the gauge object for the next pass.  Synchronises.
+void icmps_expectations(ICMPS& ic, const std::vector<int>& qn, int n1, const double* ops1, double* out1, int n2,
                         const double* ops2, double* out2, float* ms_out, cudaStream_t st);
 
 // Scale the blocks of a packed site tensor (bonds bl x br) by a per-sector vector `lam` of

@@ -112,7 +112,7 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     if (cudaDeviceSynchronize() != cudaSuccess) return DMRG_ERR_CUDA;
     for (auto& r : g_pending) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        if (r.cls >= 0 && r.cls < 4 && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             g_ms[r.cls] += ms;
             g_fl[r.cls] += r.flops;
             g_n[r.cls] += 1;
