@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--acc-m", type=int, default=500)
     ap.add_argument("--fp64-emulation", action="store_true",
                     help="FP64 grouped GEMMs on the bf16 tensor cores (FP64-accurate slicing) in the engines of "
-                         "the steps, sweeps and observe modes")
+                         "the steps, sweeps, observe and chain (FP64 runs) modes")
     ap.add_argument("--obs-m", type=int, default=800,
                     help="observe: bond dimension of the seeded state put in the inverse canonical gauge")
     ap.add_argument("--grad-L", type=int, default=128)
@@ -367,7 +367,8 @@ def chain_mode(args):
     runs = [r for r in args.chain_runs.split(",") if r] or ["fp64", args.precision]
     for run in runs:
         prec = run.split(":")[0]
-        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax, svd_fp64=run.endswith(":svd64"))
+        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax, svd_fp64=run.endswith(":svd64"),
+                        fp64_emulation=args.fp64_emulation and prec == "fp64")
         eng.set_mps(mps.bonds, data)
         dav = dict(dav_tol=1e-9, dav_max_iter=12, refine_iters=0 if prec == "fp64" else 6, serial_regions=1)
         t0 = time.perf_counter()
@@ -385,6 +386,7 @@ def chain_mode(args):
         finals[run] = rows[-1]["energy"]
         eng.close()
     out = {"mode": "chain", "L": L, "spin": args.chain_spin, "regions": args.regions, "warmup": args.chain_warmup,
+           "fp64_gemm": "emulated on bf16 tensor cores" if args.fp64_emulation else "FP64 units",
            "m_ramp": ramp, "final_energies": finals, "detail": res}
     if "fp64" in finals and args.precision in finals:
         out["dE_over_E_last_merge"] = abs(finals[args.precision] - finals["fp64"]) / abs(finals["fp64"])
