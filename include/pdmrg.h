@@ -410,7 +410,8 @@ typedef struct {
  * of FP64 rounding.  info (nullable, int[3]): beta, s and the number of FP32 accumulators per
  * problem (0, 0, 0 in mode 0).  Errors: DMRG_ERR_ARG (bad problem or segment), DMRG_ERR_STATE
  * (mode 1 without sm_103 tensor cores), DMRG_ERR_CAPACITY (mode 1 with a K too large for exact
- * FP32 accumulation, about 2 million per problem).  Synchronises the stream. */
+ * FP32 accumulation, about 2 million per problem).  Synchronises the stream; an empty batch
+ * returns DMRG_OK without any device call. */
 dmrg_status dmrg_gemm64(const dmrg_gemm_problem* probs, int n_probs, const dmrg_gemm_segment* segs, int n_segs,
                         const double* A_dev, const double* B_dev, double* C_dev, int mode, int* info,
                         void* stream);

@@ -215,6 +215,7 @@ dmrg_status dmrg_gemm64(const dmrg_gemm_problem* probs, int n_probs, const dmrg_
             g.add(p.M, p.N, p.c_off, p.sam, p.sak, p.sbn, p.sbk, p.scm, p.scn, sg, p.accumulate ? 1 : 0, p.alpha);
         }
         if (info) info[0] = info[1] = info[2] = 0;
+        if (g.empty()) return DMRG_OK;       // nothing to compute: no device call
         if (mode == 1) {
             PD_REQUIRE(tc_available(), DMRG_ERR_STATE, "FP64 emulation needs sm_103 tensor cores");
             PD_REQUIRE(run_gemm64_emu(g, A_dev, B_dev, C_dev, st), DMRG_ERR_CAPACITY,

@@ -52,3 +52,44 @@ def test_mpo_flux_rule_is_checked(lib):
     bond = pd.Bond([1, -1], {0: 1}, {0: 1}, W, [0], [0], W, [0])
     st = lib.dmrg_heff_apply(ctypes.byref(bond.desc), 0, 1, 1, 1, 1, None, None)
     assert st == 5                                                       # DMRG_ERR_QN
+
+
+def test_gauge_and_gemm_entry_points_reject_bad_arguments(lib):
+    """Host-side checks of the inverse-canonical, measurement and grouped-GEMM entry points: every
+    case below fails before any device memory is touched."""
+    import paper_1301_3494_gb300 as pd
+    fake = ctypes.c_void_p(256)           # never dereferenced: each call fails its argument checks first
+    n = ctypes.c_int(0)
+    nl = ctypes.c_longlong(0)
+    assert lib.dmrg_inverse_canonical(None) == 1
+    assert lib.dmrg_icmps_bond(None, 0, None, None, 0, ctypes.byref(n)) == 1
+    assert lib.dmrg_icmps_v(None, 0, None, 0, ctypes.byref(n)) == 1
+    assert lib.dmrg_icmps_site(None, 0, None, 0, ctypes.byref(nl)) == 1
+    assert lib.dmrg_local_expectations(None, 0, None, None, 0, None, None, None) == 1
+    P = (pd.GemmProblem * 1)()
+    S = (pd.GemmSegment * 1)()
+    P[0] = pd.GemmProblem(4, 4, 0, 1, 0, 4, 1, 4, 1, 1, 4, 0, 0, 1.0)
+    S[0] = pd.GemmSegment(0, 0, 4, 0)
+    assert lib.dmrg_gemm64(None, 1, None, 0, fake, fake, fake, 0, None, None) == 1     # no problem list
+    assert lib.dmrg_gemm64(P, 1, S, 1, fake, fake, fake, 2, None, None) == 1          # unknown mode
+    assert lib.dmrg_gemm64(P, 1, S, 1, None, fake, fake, 0, None, None) == 1          # null buffer
+    P[0] = pd.GemmProblem(4, 4, 0, 2, 0, 4, 1, 4, 1, 1, 4, 0, 0, 1.0)
+    assert lib.dmrg_gemm64(P, 1, S, 1, fake, fake, fake, 0, None, None) == 1          # segments out of range
+    P[0] = pd.GemmProblem(4, 4, 0, 1, 0, 4, 1, 4, 1, 1, 4, 0, 0, 1.0)
+    S[0] = pd.GemmSegment(0, 0, 0, 0)
+    assert lib.dmrg_gemm64(P, 1, S, 1, fake, fake, fake, 0, None, None) == 1          # K = 0
+    info = (ctypes.c_int * 3)(7, 7, 7)
+    assert lib.dmrg_gemm64(P, 0, S, 0, fake, fake, fake, 0, info, None) == 0          # empty batch: no work
+    assert list(info) == [0, 0, 0]
+
+
+def test_emulation_needs_tensor_cores(lib):
+    """Without an sm_103 GPU the emulated mode is refused (DMRG_ERR_STATE) before device access."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: covered by tests/test_gpu_emu.py")
+    import paper_1301_3494_gb300 as pd
+    fake = ctypes.c_void_p(256)
+    P = (pd.GemmProblem * 1)(pd.GemmProblem(4, 4, 0, 1, 0, 4, 1, 4, 1, 1, 4, 0, 0, 1.0))
+    S = (pd.GemmSegment * 1)(pd.GemmSegment(0, 0, 4, 0))
+    assert lib.dmrg_gemm64(P, 1, S, 1, fake, fake, fake, 1, None, None) == 8
