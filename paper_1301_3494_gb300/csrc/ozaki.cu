@@ -275,6 +275,8 @@ std::unique_ptr<EmuPlan> build_plan(const GemmBatch& g, cudaStream_t st) {
     }
     P->a_rows = sa.layout();
     P->b_rows = sb.layout();
+    PD_REQUIRE(P->a_rows < (long long)INT32_MAX && P->b_rows < (long long)INT32_MAX, DMRG_ERR_CAPACITY,
+               "emulated GEMM batch too large");
     // scale classes: rows feeding one output row (column) of one problem share a class
     UF ua((size_t)std::max<long long>(1, P->a_rows)), ub((size_t)std::max<long long>(1, P->b_rows));
     for (size_t p = 0; p < g.probs.size(); ++p) {
