@@ -103,12 +103,12 @@ class _Batch:
         Bf = np.concatenate(self.B)
         worst = 0.0
         for p, (ref, ablocks) in zip(self.probs, self.ref):
-            M, N, seg0, nseg, c_off, sam, sak, sbn, sbk, scm, scn, acc, alpha = p
+            M, N, seg0, nseg, c_off, _sam, _sak, sbn, sbk, scm, scn, _acc, alpha = p
             mm, nn = np.meshgrid(np.arange(M), np.arange(N), indexing="ij")
             got = Cflat[c_off + mm * scm + nn * scn]
             amax, bmax, ktot = np.zeros(M), np.zeros(N), 0
             for s in range(nseg):
-                a_off, b_off, K = self.segs[seg0 + s]
+                _a_off, b_off, K = self.segs[seg0 + s]
                 Am = ablocks[s][1]
                 nk, kk = np.meshgrid(np.arange(N), np.arange(K), indexing="ij")
                 Bm = Bf[b_off + nk * sbn + kk * sbk]
