@@ -214,12 +214,12 @@ dmrg_status dmrg_energy_gradient(dmrg_ctx* ctx, double* Wbar, double* E_out);
  * dmrg_set_mps.  Region mode: DMRG_ERR_STATE.  Synchronises the stream. */
 dmrg_status dmrg_get_site(dmrg_ctx* ctx, int j, double* out, long long cap, long long* n_out);
 
-/* Inverse canonical gauge of the serial state (Sec. IV, Figs. 5 and 6): a copy of the state,
+/* Inverse canonical gauge of the serial state (Sec. IV, Figs. 8 and 9): a copy of the state,
  * kept in the context, in which every site tensor psi_j = Lambda_j Gamma_j Lambda_{j+1} is an
  * orthogonality centre and every inner bond b (joining sites b-1 and b) carries the diagonal
  * V_b = Lambda_b^{-1} of inverse Schmidt weights: |Psi> = psi_0 V_1 psi_1 ... V_{L-1} psi_{L-1}.
  * Built in FP64 (any precision mode) by untruncated SVDs: the centre is moved to site 0, then
- * Fig. 5's step (SVD, one copy of Lambda into each neighbour, V on the bond) is taken at every
+ * Fig. 8's step (SVD, one copy of Lambda into each neighbour, V on the bond) is taken at every
  * bond left to right; Schmidt values at or below 1e-12 of the largest are dropped so that V is
  * finite.  The engine's own state is not changed; a later set_mps, sweep, advance, region set-up
  * or merge discards the copy.  Region mode: DMRG_ERR_STATE.  Synchronises the stream. */
@@ -292,6 +292,9 @@ typedef struct {
     long long svd_fp64_fallbacks; /* FP32 splits redone in FP64 (re-orthonormalisation refused)  */
     double svd_block_flops;      /* FP32 Gram + column-rotation flops of the block-Jacobi splits */
     long long svd_rot_hist[48];  /* block Jacobi: block pairs rotated in sweep i, summed over splits */
+    long long emu_fallbacks;     /* emulated FP64 GEMM batches sent to the FP64 units by the scale
+                                    guard (a shared operand row's scale class far above a problem's
+                                    own row maximum) or by a NaN/Inf operand                     */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);
@@ -407,8 +410,12 @@ typedef struct {
  * operand row is scaled by a power of two and cut into s slices of beta bits, the slice
  * products are summed exactly in FP32 on the tensor cores and combined in FP64; the error is
  * below (s^2/2 + 2) 2^(-s beta) max_k|A(m,k)| max_k|B(n,k)| per term (s beta >= 56), at the level
- * of FP64 rounding.  info (nullable, int[3]): beta, s and the number of FP32 accumulators per
- * problem (0, 0, 0 in mode 0).  Errors: DMRG_ERR_ARG (bad problem or segment), DMRG_ERR_STATE
+ * of FP64 rounding.  Operand rows that several problems share get one scale, that of the largest
+ * row they meet in any problem; when a problem's own row (column) maximum lies more than 3 bits
+ * below that scale, or an operand is NaN or Inf, the whole batch runs on the FP64 units instead
+ * (counted in dmrg_profile.emu_fallbacks).  info (nullable, int[3]): beta, s and the number of
+ * FP32 accumulators per problem (0, 0, 0 in mode 0 and when the batch ran on the FP64 units).
+ * Errors: DMRG_ERR_ARG (bad problem or segment), DMRG_ERR_STATE
  * (mode 1 without sm_103 tensor cores), DMRG_ERR_CAPACITY (mode 1 with a K too large for exact
  * FP32 accumulation, about 2 million per problem).  Synchronises the stream; an empty batch
  * returns DMRG_OK without any device call. */

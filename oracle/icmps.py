@@ -1,6 +1,6 @@
 """Inverse canonical MPS gauge and local expectation values (Sec. IV) -- test infrastructure.
 
-The gauge (Sec. IV, Figs. 5 and 6): every site tensor psi_j is an orthogonality centre (OC) and
+The gauge (Sec. IV, Figs. 8 and 9): every site tensor psi_j is an orthogonality centre (OC) and
 every inner bond b carries the diagonal V_b = Lambda_b^-1 of inverse Schmidt weights, so that the
 state is psi_0 V_1 psi_1 V_2 ... V_{L-1} psi_{L-1}, with psi_j = Lambda_j Gamma_j Lambda_{j+1}
 in the Gamma-Lambda (canonical) notation.  Bond b sits between sites b-1 and b; bonds 0 and L
@@ -42,7 +42,7 @@ def inverse_canonical(sites, bonds, qn):
     for j in range(L - 1):
         theta = O.two_site(psi[j], psi[j + 1], qn)
         A, lam, B, mid, _ = O.split_two_site(theta, bonds[j], bonds[j + 2], qn, m_max=1 << 60)
-        # one copy of Lambda into each neighbour, V = Lambda^-1 on the bond (Fig. 5)
+        # one copy of Lambda into each neighbour, V = Lambda^-1 on the bond (Fig. 8)
         psi[j] = {(qa, s): blk * lam[qa + qn[s]][None, :] for (qa, s), blk in A.items()}
         psi[j + 1] = {(qm, s): lam[qm][:, None] * blk for (qm, s), blk in B.items()}
         V[j + 1] = {q: 1.0 / v for q, v in lam.items()}

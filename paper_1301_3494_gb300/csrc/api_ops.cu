@@ -218,9 +218,24 @@ dmrg_status dmrg_gemm64(const dmrg_gemm_problem* probs, int n_probs, const dmrg_
         if (g.empty()) return DMRG_OK;       // nothing to compute: no device call
         if (mode == 1) {
             PD_REQUIRE(tc_available(), DMRG_ERR_STATE, "FP64 emulation needs sm_103 tensor cores");
-            PD_REQUIRE(run_gemm64_emu(g, A_dev, B_dev, C_dev, st), DMRG_ERR_CAPACITY,
-                       "K too large for exact FP32 accumulation");
-            if (info) emu_plan_info(g, info, info + 1, info + 2);
+            if (run_gemm64_emu(g, A_dev, B_dev, C_dev, st)) {
+                if (info) emu_plan_info(g, info, info + 1, info + 2);
+            } else {
+                // a plan that exists but was not run: its scale guard sent the batch to the FP64
+                // units (info stays 0); no plan: K is too large for exact FP32 accumulation
+                int beta = 0, s = 0, groups = 0;
+                emu_plan_info(g, &beta, &s, &groups);
+                PD_REQUIRE(beta > 0, DMRG_ERR_CAPACITY, "K too large for exact FP32 accumulation");
+                const int saved = g_gemm64_emu;
+                g_gemm64_emu = 0;
+                try {
+                    run_gemm64(g, A_dev, B_dev, C_dev, st);
+                } catch (...) {
+                    g_gemm64_emu = saved;
+                    throw;
+                }
+                g_gemm64_emu = saved;
+            }
         } else {
             const int saved = g_gemm64_emu;
             g_gemm64_emu = 0;

@@ -1,4 +1,4 @@
-// Inverse canonical MPS gauge and local expectation values (Sec. IV, Figs. 5 and 6).
+// Inverse canonical MPS gauge and local expectation values (Sec. IV, Figs. 8 and 9).
 //
 // Gauge: psi_j = Lambda_j Gamma_j Lambda_{j+1} on every site and V_b = Lambda_b^-1 on every inner
 // bond b (bond b joins sites b-1 and b), so that the state is psi_0 V_1 psi_1 ... V_{L-1} psi_{L-1}
@@ -8,7 +8,7 @@
 //       U Lambda absorbed into site j-1 (OC moves to site 0);
 //   (2) 0, 1, ..., L-2: site j viewed as rows (a, s) x cols b = U Lambda W^T; psi_j <- U Lambda,
 //       V_{j+1} <- Lambda^-1, Lambda W^T absorbed into site j+1.
-// Pass (2) is Fig. 5's Lambda-V-Lambda step repeated at every bond: with site j+1 right-orthonormal,
+// Pass (2) is Fig. 8's Lambda-V-Lambda step repeated at every bond: with site j+1 right-orthonormal,
 // the SVD of the two-site Theta = psi_j B_{j+1} and that of psi_j share U and Lambda.  Singular
 // values at or below 1e-12 of the largest are dropped so that V stays finite.
 //

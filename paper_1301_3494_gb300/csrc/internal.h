@@ -56,6 +56,8 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops);
 void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist);
 // An FP32 split redone in FP64 (counted always, not only while profiling).
 void prof_fallback();
+// An emulated FP64 GEMM batch sent to the FP64 units by its scale guard (counted always).
+void prof_emu_fallback();
 
 // Persistent and cooperative grids are sized to the SMs of the device; while R regions run
 // concurrently (one host thread each), each thread caps its grids at sms / R so that the regions

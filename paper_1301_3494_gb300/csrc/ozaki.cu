@@ -16,7 +16,12 @@
 //
 // Rows that meet in one accumulator must share their scale: the rows of all segments of one
 // problem that produce the same output row (and column) are merged into one scale class
-// (union-find over operand rows), and a class's exponent is that of its largest entry.
+// (union-find over operand rows), and a class's exponent is that of its largest entry.  Operand
+// blocks are stored once however many problems use them, so a class can also hold rows of other
+// problems; the error bound then refers to the class maximum instead of the problem's own.  Before
+// any slicing, a check compares, for every problem and output row (column), the exponent of its
+// own largest operand entry with its class exponent; a gap above kGuardBits, or a NaN/Inf operand,
+// sends the whole batch to the FP64 units (which also propagate NaN and Inf as FP64 would).
 //
 // Accumulators: one per slice pair ("pair" mode) or one per pair level i + j ("level" mode,
 // fewer FP32 outputs, but more terms per accumulator and so a smaller beta); the mode and beta
@@ -34,6 +39,7 @@ thread_local int g_gemm64_emu = 0;
 
 struct EmuPlan {
     size_t nprobs = 0;                 // batch size the plan was built for
+    unsigned long long key = 0;        // hash of the batch's problems and segments
     bool usable = false;
     int beta = 0, s = 0, ngroups = 0;
     int lda = 64, ldb = 64;
@@ -42,6 +48,8 @@ struct EmuPlan {
     int nsplit_chunks = 0, ncomb_chunks = 0, na_cls = 0, nb_cls = 0;
     GemmBatch tc;
     DBuf split, comb, chunks_s, chunks_c, cls_a, cls_b, cmax, slab_a, slab_b, tmp, gshift, err;
+    DBuf rowmax, chk, chk_rows, flag;  // per-row maxima, per-problem check jobs, guard flag
+    int nchk = 0;
     double hi_unit = 1.0, lo_unit = 1.0;   // 2^(-l_mid beta), 2^(-(s+1) beta)
     double est_ms = 0.0;
 };
@@ -70,24 +78,34 @@ struct CombJob {
     double alpha;
 };
 constexpr int kChunk = 16384;
+// largest gap (bits) between a problem's own row maximum and its scale class maximum
+constexpr int kGuardBits = 3;
 
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(fabs(x));
 }
 
-// class maxima: cmax[cls[row]] = max |x| over the row's K entries (bit patterns of nonnegative
-// doubles order like unsigned integers).  Chunks start at multiples of kChunk and rows are ld
-// (a multiple of 64) long, so the 32 elements a warp takes at a time lie in one row: one atomic
-// per warp.
+// exponent e of a class maximum mx = f 2^e, f in [0.5, 1) (every entry of the class is below 2^e)
+__device__ __forceinline__ int class_exp(unsigned long long bits) {
+    const int E = (int)((bits >> 52) & 0x7FF);
+    if (E != 0) return E - 1022;
+    int e = 0;
+    const double mx = __longlong_as_double((long long)bits);
+    if (mx > 0.0) frexp(mx, &e);          // subnormal maximum
+    return e;
+}
+
+// row maxima: rowmax[side_base + row] = max |x| over the row's K entries (bit patterns of
+// nonnegative doubles order like unsigned integers; A rows first, then B rows).  Chunks start at
+// multiples of kChunk and rows are ld (a multiple of 64) long, so the 32 elements a warp takes at a
+// time lie in one row: one atomic per warp.
 __global__ void k_oz_absmax(const SplitJob* __restrict__ jobs, const Chunk* __restrict__ chunks,
-                            const double* __restrict__ A, const double* __restrict__ B, const int* __restrict__ cls_a,
-                            const int* __restrict__ cls_b, int na_cls, unsigned long long* __restrict__ cmax,
-                            int ld_a, int ld_b) {
+                            const double* __restrict__ A, const double* __restrict__ B, long long a_rows,
+                            unsigned long long* __restrict__ rowmax, int ld_a, int ld_b) {
     const Chunk c = chunks[blockIdx.x];
     const SplitJob j = jobs[c.job];
     const double* X = j.which ? B : A;
-    const int* cls = j.which ? cls_b : cls_a;
-    unsigned long long* mx = cmax + (j.which ? na_cls : 0);
+    unsigned long long* mx = rowmax + (j.which ? a_rows : 0);
     const int ld = j.which ? ld_b : ld_a;
     const int lane = threadIdx.x & 31;
     for (int base = threadIdx.x - lane; base < c.len; base += blockDim.x) {      // c.len: a multiple of 64
@@ -100,18 +118,47 @@ __global__ void k_oz_absmax(const SplitJob* __restrict__ jobs, const Chunk* __re
             const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
             v = w > v ? w : v;
         }
-        if (lane == 0 && v != 0) atomicMax(mx + cls[j.row0 + m], v);
+        if (lane == 0 && v != 0) atomicMax(mx + j.row0 + m, v);
     }
 }
 
-// exponent e of a class maximum mx = f 2^e, f in [0.5, 1) (every entry of the class is below 2^e)
-__device__ __forceinline__ int class_exp(unsigned long long bits) {
-    const int E = (int)((bits >> 52) & 0x7FF);
-    if (E != 0) return E - 1022;
-    int e = 0;
-    const double mx = __longlong_as_double((long long)bits);
-    if (mx > 0.0) frexp(mx, &e);          // subnormal maximum
-    return e;
+// class maxima from row maxima (cmax[cls[r]] over the rows of both sides; B classes follow the
+// na_cls A classes); a NaN or Inf anywhere (exponent field 0x7FF) sets bit 2 of *flag.
+__global__ void k_oz_classmax(const unsigned long long* __restrict__ rowmax, long long a_rows, long long rows,
+                              const int* __restrict__ cls_a, const int* __restrict__ cls_b, int na_cls,
+                              unsigned long long* __restrict__ cmax, unsigned* __restrict__ flag) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long v = rowmax[r];
+        if (v == 0) continue;
+        if (((v >> 52) & 0x7FF) == 0x7FF) atomicOr(flag, 2u);
+        const int c = r < a_rows ? cls_a[r] : na_cls + cls_b[r - a_rows];
+        atomicMax(cmax + c, v);
+    }
+}
+
+// one output row (A side) or column (B side) of one problem: the slab rows of its segments
+struct ChkJob {
+    int n, nseg, seg0, which;   // rows (M or N), segments, first entry in chk_rows, side
+};
+// For every row m of a job: own = max over its segments of rowmax[row0_s + m]; a class exponent
+// more than guard bits above own's sets bit 1 of *flag (the batch then runs on the FP64 units).
+__global__ void k_oz_check(const ChkJob* __restrict__ jobs, const long long* __restrict__ chk_rows,
+                           const unsigned long long* __restrict__ rowmax, long long a_rows,
+                           const int* __restrict__ cls_a, const int* __restrict__ cls_b, int na_cls,
+                           const unsigned long long* __restrict__ cmax, int guard, unsigned* __restrict__ flag) {
+    const ChkJob j = jobs[blockIdx.x];
+    const long long base = j.which ? a_rows : 0;
+    for (int m = threadIdx.x; m < j.n; m += blockDim.x) {
+        unsigned long long own = 0;
+        for (int s = 0; s < j.nseg; ++s) {
+            const unsigned long long v = rowmax[base + chk_rows[j.seg0 + s] + m];
+            own = v > own ? v : own;
+        }
+        if (own == 0) continue;          // an all-zero row contributes nothing
+        const long long r0 = chk_rows[j.seg0] + m;
+        const unsigned long long cm = cmax[j.which ? na_cls + cls_b[r0] : cls_a[r0]];
+        if (class_exp(cm) - class_exp(own) > guard) atomicOr(flag, 1u);
+    }
 }
 
 // slices: slab[(i * rows + row0 + m) * ld + k] = a_i for k < K, 0 for K <= k < ld.  Integer
@@ -250,9 +297,22 @@ void chunk_jobs(const std::vector<long long>& sizes, std::vector<Chunk>& out) {
             out.push_back({(int)j, (int)e, (int)std::min<long long>(kChunk, sizes[j] - e), 0});
 }
 
+// FNV-1a over the problem and segment lists: a plan is reused only for the batch it was built for.
+unsigned long long batch_key(const GemmBatch& g) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    if (!g.probs.empty()) mix(g.probs.data(), g.probs.size() * sizeof(GProb));
+    if (!g.segs.empty()) mix(g.segs.data(), g.segs.size() * sizeof(GSeg));
+    return h;
+}
+
 std::unique_ptr<EmuPlan> build_plan(const GemmBatch& g, cudaStream_t st) {
     std::unique_ptr<EmuPlan> P(new EmuPlan());
     P->nprobs = g.probs.size();
+    P->key = batch_key(g);
     Side sa, sb;
     std::vector<std::vector<int>> pa(g.probs.size()), pb(g.probs.size());   // block ids per segment
     long long kmax_tot = 0;
@@ -300,6 +360,16 @@ std::unique_ptr<EmuPlan> build_plan(const GemmBatch& g, cudaStream_t st) {
         return c;
     };
     const std::vector<int> ca = classes(ua, P->a_rows, &P->na_cls), cb = classes(ub, P->b_rows, &P->nb_cls);
+    // guard jobs: every problem's output rows (A side) and columns (B side)
+    std::vector<ChkJob> chk;
+    std::vector<long long> chk_rows;
+    for (size_t p = 0; p < g.probs.size(); ++p) {
+        const GProb& q = g.probs[p];
+        chk.push_back({q.M, (int)pa[p].size(), (int)chk_rows.size(), 0});
+        for (int b : pa[p]) chk_rows.push_back(sa.row0[b]);
+        chk.push_back({q.N, (int)pb[p].size(), (int)chk_rows.size(), 1});
+        for (int b : pb[p]) chk_rows.push_back(sb.row0[b]);
+    }
     // mode and beta
     struct Opt { bool level; int beta, s, groups, pairs; double ms; };
     Opt best{false, 0, 0, 0, 0, -1.0};
@@ -394,6 +464,11 @@ std::unique_ptr<EmuPlan> build_plan(const GemmBatch& g, cudaStream_t st) {
     upload(P->cls_a, ca, st);
     upload(P->cls_b, cb, st);
     upload(P->gshift, gshift, st);
+    upload(P->chk, chk, st);
+    upload(P->chk_rows, chk_rows, st);
+    P->nchk = (int)chk.size();
+    P->rowmax.ensure((size_t)std::max<long long>(1, P->a_rows + P->b_rows) * 8, st);
+    P->flag.ensure(4, st);
     P->cmax.ensure((size_t)(P->na_cls + P->nb_cls) * 8, st);
     P->slab_a.ensure((size_t)std::max<long long>(1, P->a_rows * P->s) * P->lda * 2, st);
     P->slab_b.ensure((size_t)std::max<long long>(1, P->b_rows * P->s) * P->ldb * 2, st);
@@ -415,15 +490,38 @@ void free_emu_plan(EmuPlan* p) { delete p; }
 bool run_gemm64_emu(GemmBatch& g, const double* A, const double* B, double* C, cudaStream_t st) {
     if (g.empty()) return true;
     if (!tc_available()) return false;
-    if (!g.emu || g.emu->nprobs != g.probs.size()) g.emu.reset(build_plan(g, st).release(), free_emu_plan);
+    const unsigned long long key = batch_key(g);
+    if (!g.emu || g.emu->nprobs != g.probs.size() || g.emu->key != key)
+        g.emu.reset(build_plan(g, st).release(), free_emu_plan);
     EmuPlan& P = *g.emu;
     if (!P.usable) return false;
     void* tok = prof_on() ? prof_start(st) : nullptr;
+    PD_CK(cudaMemsetAsync(P.rowmax.p, 0, (size_t)std::max<long long>(1, P.a_rows + P.b_rows) * 8, st));
     PD_CK(cudaMemsetAsync(P.cmax.p, 0, (size_t)(P.na_cls + P.nb_cls) * 8, st));
+    PD_CK(cudaMemsetAsync(P.flag.p, 0, 4, st));
+    PD_CK(cudaMemsetAsync(P.err.p, 0, 4, st));
     k_oz_absmax<<<(unsigned)P.nsplit_chunks, 256, 0, st>>>(P.split.as<SplitJob>(), P.chunks_s.as<Chunk>(), A, B,
-                                                           P.cls_a.as<int>(), P.cls_b.as<int>(), P.na_cls,
-                                                           P.cmax.as<unsigned long long>(), P.lda, P.ldb);
+                                                           P.a_rows, P.rowmax.as<unsigned long long>(), P.lda, P.ldb);
     PD_LAUNCHED();
+    const long long rows = P.a_rows + P.b_rows;
+    k_oz_classmax<<<(unsigned)std::min<long long>(1024, (rows + 255) / 256), 256, 0, st>>>(
+        P.rowmax.as<unsigned long long>(), P.a_rows, rows, P.cls_a.as<int>(), P.cls_b.as<int>(), P.na_cls,
+        P.cmax.as<unsigned long long>(), P.flag.as<unsigned>());
+    PD_LAUNCHED();
+    k_oz_check<<<(unsigned)P.nchk, 128, 0, st>>>(P.chk.as<ChkJob>(), P.chk_rows.as<long long>(),
+                                                 P.rowmax.as<unsigned long long>(), P.a_rows, P.cls_a.as<int>(),
+                                                 P.cls_b.as<int>(), P.na_cls, P.cmax.as<unsigned long long>(),
+                                                 kGuardBits, P.flag.as<unsigned>());
+    PD_LAUNCHED();
+    unsigned flag = 0;
+    PD_CK(cudaMemcpyAsync(&flag, P.flag.p, 4, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    if (flag) {
+        // a class maximum far above a problem's own, or a non-finite operand: FP64 units
+        if (tok) prof_stop(tok, st, PROF_NONE, 0.0);
+        prof_emu_fallback();
+        return false;
+    }
     k_oz_split<<<(unsigned)P.nsplit_chunks, 256, 0, st>>>(
         P.split.as<SplitJob>(), P.chunks_s.as<Chunk>(), A, B, P.cls_a.as<int>(), P.cls_b.as<int>(), P.na_cls,
         P.cmax.as<unsigned long long>(), P.slab_a.as<__nv_bfloat16>(), P.slab_b.as<__nv_bfloat16>(), P.a_rows,

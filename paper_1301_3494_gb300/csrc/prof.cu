@@ -33,6 +33,7 @@ int* sweep_flags_host(int n) {
 
 std::atomic<long long> g_launches{0};
 std::atomic<long long> g_fallbacks{0};
+std::atomic<long long> g_emu_fallbacks{0};
 thread_local int g_prof_class = PROF_MV;
 
 namespace {
@@ -54,6 +55,7 @@ long long g_n[4] = {0, 0, 0, 0};
 bool prof_on() { return g_on.load(std::memory_order_relaxed); }
 
 void prof_fallback() { g_fallbacks.fetch_add(1); }
+void prof_emu_fallback() { g_emu_fallbacks.fetch_add(1); }
 
 void* prof_start(cudaStream_t st) {
     cudaEvent_t* ev = new cudaEvent_t[2];
@@ -104,6 +106,7 @@ void dmrg_profile_reset(void) {
     for (auto& x : g_rot_hist) x = 0;
     g_launches.store(0);
     g_fallbacks.store(0);
+    g_emu_fallbacks.store(0);
 }
 
 dmrg_status dmrg_profile_read(dmrg_profile* out) {
@@ -145,6 +148,7 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->svd_fp64_fallbacks = g_fallbacks.load();
     out->svd_block_flops = g_svd_block_flops;
     for (int i = 0; i < 48; ++i) out->svd_rot_hist[i] = g_rot_hist[i];
+    out->emu_fallbacks = g_emu_fallbacks.load();
     return DMRG_OK;
 }
 

@@ -165,3 +165,55 @@ def test_state_export_round_trip():
     assert all(eng2.bond(b) == bonds[b] for b in range(L + 1))
     eng.close()
     eng2.close()
+
+
+@pytest.mark.parametrize("R", [2, 4])
+def test_regions_cylinder_serial_schedule(R):
+    """6x4 Heisenberg cylinder (2-D snake MPO, D = 14), m = 128, the regions of each Fig. 4 phase
+    driven one after another by the calling thread (serial_regions = 1, cooperative Jacobi
+    launches inside the regions): region centres, sweep energies, merge fidelities and every
+    region's bond tables match the FP64 oracle sweep by sweep."""
+    mpo = wl.heisenberg_square_cylinder(6, 4)
+    qn = list(mpo.site.qn)
+    mps = wl.random_mps(mpo.L, qn, 0, 16, seed=2)
+    ref = P.ParallelDMRG(mpo, mps, R)
+    ref.setup(64, warmup_sweeps=1)
+    eng = engine_for(pd, mpo)
+    load_mps(eng, mps, qn)
+    eng.setup_regions(R, 1, 64, serial_regions=1)
+    for k in range(R):
+        assert eng.center(k) == ref.regions[k].oc
+    for sweep, m in enumerate((128, 128)):
+        r = ref.sweep(m)
+        g = eng.sweep(m, serial_regions=1)
+        assert abs(g["energy"] - r["energy"]) <= TOL * abs(r["energy"]), sweep
+        fids = [x["fidelity"] for x in r["merges"]]
+        assert abs(g["max_fidelity"] - max(fids)) <= 1e-7, (g["max_fidelity"], fids)
+        assert abs(g["min_fidelity"] - min(fids)) <= 1e-7, (g["min_fidelity"], fids)
+    for k, reg in enumerate(ref.regions):
+        assert eng.center(k) == reg.oc
+        for b in range(reg.p + 1, reg.q + 1):
+            assert eng.bond(b) == reg.bonds[b], (k, b)
+    eng.close()
+
+
+def test_regions_cylinder_serial_schedule_bf16():
+    """The bench's code path on a 2-D MPO: bf16 tensor-core matvec with FP32 refinement, FP32
+    block-Jacobi splits (cooperative launch) on ordinary bonds, FP64 accurate splits and merges at
+    the shared bonds, 4 regions on the serial schedule.  The final parallel-sweep energy agrees
+    with the FP64 oracle's converged serial energy of the 6x4 cylinder at m = 128 to 2e-5
+    (FP32 environments bias the mixed engine's own Rayleigh quotient at the 1e-5 level)."""
+    mpo = wl.heisenberg_square_cylinder(6, 4)
+    qn = list(mpo.site.qn)
+    mps = wl.random_mps(mpo.L, qn, 0, 16, seed=2)
+    ref = O.SerialDMRG(mpo, mps)
+    for m in (64, 128, 128, 128):
+        r = ref.sweep(m)
+    eng = engine_for(pd, mpo, precision="bf16")
+    load_mps(eng, mps, qn)
+    dav = dict(dav_tol=1e-9, dav_max_iter=12, refine_iters=6, serial_regions=1)
+    eng.setup_regions(4, 1, 64, **dav)
+    for m in (128, 128, 128, 128):
+        g = eng.sweep(m, **dav)
+    assert abs(g["energy"] - r["energy"]) <= 2e-5 * abs(r["energy"]), (g["energy"], r["energy"])
+    eng.close()

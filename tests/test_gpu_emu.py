@@ -201,3 +201,53 @@ def test_emulated_local_expectations_match_oracle():
     assert np.abs(e1 - e1_o).max() <= 1e-12
     assert np.abs(e2 - e2_o).max() <= 1e-12
     eng.close()
+
+
+def _two_problem_batch(scale_z, nan=False):
+    """Two problems of two segments each share the A block X; X meets Y (magnitude 1) in the
+    first and Z (magnitude scale_z) in the second, so X's rows share one scale class with both.
+    Returns flat A, B, the problem and segment tuples and the exact products."""
+    rng = np.random.default_rng(11)
+    M, N, K = 40, 30, 70
+    X, Y, Z = rng.standard_normal((M, K)), rng.standard_normal((M, K)), rng.standard_normal((M, K)) * scale_z
+    if nan:
+        Z[3, 5] = np.nan
+    Bs = [rng.standard_normal((N, K)) for _ in range(4)]
+    A = np.concatenate([X.ravel(), Y.ravel(), Z.ravel()])
+    B = np.concatenate([b.ravel() for b in Bs])
+    segs = [(0, 0, K), (M * K, N * K, K), (0, 2 * N * K, K), (2 * M * K, 3 * N * K, K)]
+    probs = [(M, N, 0, 2, 0, K, 1, K, 1, N, 1, 0, 1.0), (M, N, 2, 2, M * N, K, 1, K, 1, N, 1, 0, 1.0)]
+    ref = [X @ Bs[0].T + Y @ Bs[1].T, X @ Bs[2].T + Z @ Bs[3].T]
+    bound = [2 * K * 2.0 ** -52 * np.outer(np.maximum(np.abs(X).max(1), np.abs(Y).max(1)),
+                                           np.maximum(np.abs(Bs[0]).max(1), np.abs(Bs[1]).max(1)))]
+    return A, B, probs, segs, ref, bound
+
+
+def test_emulated_gemm_shared_block_with_unequal_partners():
+    """A block shared by two problems whose other operands differ by 1e10 in magnitude: the first
+    problem must still be FP64-accurate relative to its own rows (its scale class is inflated by
+    the second problem's rows, so the batch goes to the FP64 units); equal partners stay emulated."""
+    for scale_z, emulated in ((1e10, False), (1.0, True)):
+        A, B, probs, segs, ref, bound = _two_problem_batch(scale_z)
+        Ad, Bd = torch.as_tensor(A).cuda(), torch.as_tensor(B).cuda()
+        Cd = torch.zeros(2 * 40 * 30, dtype=torch.float64, device="cuda")
+        pd.profile_reset()
+        info = pd.gemm64(probs, segs, Ad.data_ptr(), Bd.data_ptr(), Cd.data_ptr(), 1)
+        fb = pd.profile_read()["emu_fallbacks"]
+        C = Cd.cpu().numpy()
+        got0 = C[:1200].reshape(40, 30)
+        assert np.all(np.abs(got0 - ref[0]) <= bound[0]), np.abs(got0 - ref[0]).max()
+        got1 = C[1200:].reshape(40, 30)
+        assert np.allclose(got1, ref[1], rtol=1e-13, atol=1e-13 * np.abs(ref[1]).max())
+        assert (info[0] > 0) == emulated and fb == (0 if emulated else 1), (info, fb)
+
+
+def test_emulated_gemm_propagates_nan():
+    A, B, probs, segs, ref, _ = _two_problem_batch(1.0, nan=True)
+    Ad, Bd = torch.as_tensor(A).cuda(), torch.as_tensor(B).cuda()
+    Cd = torch.zeros(2 * 40 * 30, dtype=torch.float64, device="cuda")
+    info = pd.gemm64(probs, segs, Ad.data_ptr(), Bd.data_ptr(), Cd.data_ptr(), 1)
+    C = Cd.cpu().numpy()
+    assert info == (0, 0, 0)
+    assert np.isnan(C[1200:].reshape(40, 30)[3]).all()          # row 3 of the second problem
+    assert np.isfinite(C[:1200]).all()

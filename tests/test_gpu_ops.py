@@ -216,11 +216,16 @@ def test_svd_split_fp32_block_jacobi(kind, m, mmax):
 
 
 # ------------------------------------------------------------------------------------------
-# Tensor-core (tcgen05) paths: normwise relative error against the FP64 oracle.  Bounds from
-# the operand rounding: bf16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3; psi, L, R and
-# the MPO-mixed intermediate are rounded once each), tf32 keeps 11 (2^-11 ~ 5e-4, truncation).
+# Tensor-core (tcgen05) paths against the FP64 oracle, element by element and normwise.  Every
+# product term L W1 W2 R x of an output element passes through at most four operand roundings
+# (x, L and R to the operand type, the MPO-mixed intermediate Y to it as well) and FP32
+# accumulation, so |y - y_ref| <= c u (|L| |W1| |W2| |R| |x|) elementwise, the right side being the
+# oracle applied to absolute values; u = 2^-8 for bf16 (8 significant bits, round to nearest) and
+# 2^-10 for tf32 (11 bits, the conversion may truncate), c = 8 (four roundings, twice over for
+# margin; FP32 accumulation adds K 2^-24, below 1e-3 u).  Normwise: 2e-2 (bf16), 5e-3 (tf32).
 # ------------------------------------------------------------------------------------------
 TC_TOL = {pd.BF16: 2e-2, pd.TF32: 5e-3}
+TC_UNIT = {pd.BF16: 2.0 ** -8, pd.TF32: 2.0 ** -10}
 
 
 def _nrel(got, ref):
@@ -249,6 +254,17 @@ def test_heff_apply_tensor_core(prec, kind, m):
     err = _nrel(got, ref)
     assert err <= TC_TOL[prec], err
     assert err > 0.0        # the tensor-core path really ran in reduced precision
+    # element-wise: a wrong or mis-scattered block of small norm fails here
+    absref = O.heff_apply({k: np.abs(v) for k, v in Lenv.items()}, np.abs(W1), f0, np.abs(W2), f2,
+                          {k: np.abs(v) for k, v in Renv.items()}, {k: np.abs(v) for k, v in psi.items()}, qn)
+    worst = 0.0
+    for k in ref:
+        bound = 8.0 * TC_UNIT[prec] * absref[k] + 1e-300
+        e = np.abs(got[k] - ref[k])
+        worst = max(worst, float((e / bound).max()))
+        assert np.all(e <= bound), (k, worst)
+    for k in set(got) - set(ref):        # blocks with no contributing term stay exactly zero
+        assert not np.any(got[k]), k
 
 
 @pytest.mark.parametrize("kind,m", [("chain", 500), ("cyl", 800)])
