@@ -61,6 +61,10 @@ def parse():
                          "accuracy: the same serial sweeps (m ramped to --acc-m) in FP64 and in --precision "
                          "mode from the same seeded state, energies and sweep times compared")
     ap.add_argument("--acc-m", type=int, default=500)
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="sweeps mode: skip the FP64 evaluation and the FP64-vs-mixed same-state sweeps")
+    ap.add_argument("--svd-plain-jacobi", action="store_true",
+                    help="splits by the one-sided Jacobi on the sector matrices (no QR preconditioning)")
     ap.add_argument("--fp64-emulation", action="store_true",
                     help="FP64 grouped GEMMs on the bf16 tensor cores (FP64-accurate slicing) in the engines of "
                          "the steps, sweeps, observe and chain (FP64 runs) modes")
@@ -393,6 +397,60 @@ def chain_mode(args):
     print(json.dumps(out))
 
 
+def accuracy_leg(args, eng, W, flux, D, qn):
+    """The accuracy half of the metric, after the timed sweeps: (1) the timed engine's state,
+    exported as one MPS (the regions joined by V = Lambda^-1 at every boundary, Eq. (merge)), is
+    canonicalised and evaluated by an FP64 engine; (2) from that canonical state, one FP64 serial
+    sweep and one mixed-precision serial sweep (same m, same Davidson iteration count: the mixed
+    sweep's tensor-core iterations plus its FP32 refinement), both timed; the mixed result is
+    evaluated by an FP64 engine.  Returns the record for the JSON line."""
+    import torch
+    import paper_1301_3494_gb300 as pd
+    emu = True      # FP64 GEMMs of the FP64 engines on the tensor cores (FP64-accurate)
+    t0 = time.perf_counter()
+    if args.mode == "sweeps":
+        bonds, data = eng.region_state()
+    else:
+        bonds, data, _ = eng.state()
+    f64 = pd.Engine(W, flux, D, qn, 0, "fp64", args.kmax, fp64_emulation=emu)
+    f64.set_mps(bonds, data)                     # canonicalised by the engine (FP64 SVDs)
+    e_state = f64.energy()
+    b0, d0, c0 = f64.state()
+    t_canon = time.perf_counter() - t0
+    iters = args.dav_iters + args.refine_iters
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    f64.sweep(args.m, dav_tol=0.0, dav_max_iter=iters, refine_iters=0)
+    torch.cuda.synchronize()
+    fp64_s = time.perf_counter() - t
+    e_fp64 = f64.energy()
+    f64.close()
+    mx = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
+    mx.set_mps(b0, d0, center=c0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    mx.sweep(args.m, dav_tol=0.0, dav_max_iter=args.dav_iters, refine_iters=args.refine_iters)
+    torch.cuda.synchronize()
+    mixed_s = time.perf_counter() - t
+    b1, d1, c1 = mx.state()
+    e_mixed_own = mx.energy()
+    mx.close()
+    ev = pd.Engine(W, flux, D, qn, 0, "fp64", args.kmax, fp64_emulation=emu)
+    ev.set_mps(b1, d1, center=c1)
+    e_mixed = ev.energy()
+    ev.close()
+    return {
+        "E_fp64_eval_of_timed_state": e_state,
+        "same_state_sweep": {
+            "E_start": e_state, "E_fp64": e_fp64, "E_mixed_fp64_eval": e_mixed, "E_mixed_own_environments": e_mixed_own,
+            "dE_over_E": abs(e_mixed - e_fp64) / abs(e_fp64), "fp64_sweep_s": fp64_s, "mixed_sweep_s": mixed_s,
+            "speedup": fp64_s / mixed_s, "schedule": "serial sweep (L - 1 steps right, L - 1 left), both precisions",
+            "davidson": f"FP64: {iters} iterations; mixed: {args.dav_iters} tensor-core + {args.refine_iters} FP32-accurate",
+            "fp64_gemm": "emulated on bf16 tensor cores (FP64-accurate)" if emu else "FP64 units"},
+        "canonicalise_and_evaluate_s": t_canon,
+    }
+
+
 def workload(args):
     if args.lattice == "triangular":
         mpo = wl.heisenberg_triangular_cylinder(args.lx, args.ly)
@@ -624,7 +682,8 @@ def main():
         chain_mode(args)
         return
     W, flux, D = wl.pack_mpo(mpo)
-    eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax, fp64_emulation=args.fp64_emulation)
+    eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax, fp64_emulation=args.fp64_emulation,
+                    svd_plain_jacobi=args.svd_plain_jacobi)
     data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
     t_setup = time.perf_counter()
     eng.set_mps(mps.bonds, data, center=center)
@@ -726,6 +785,7 @@ def main():
                                        if args.mode == "sweeps" else None),
                    "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
                    "fp64_gemm": "emulated on bf16 tensor cores" if args.fp64_emulation else "FP64 units",
+                   "svd": "one-sided Jacobi on W" if args.svd_plain_jacobi else "one-sided Jacobi on R^T (Householder QR)",
                    "setup_s": t_setup},
         "sweep_s": ms_step / 1e3 if args.mode == "sweeps" else ms_step * 2 * (L - 1) / 1e3,
         "sweep_s_note": ("one real-space parallel sweep, measured" if args.mode == "sweeps"
@@ -752,6 +812,8 @@ def main():
         "gpu_launches": prof["launches"],
         "clocks": clocks,
     }
+    if rank == 0 and args.mode in ("sweeps", "steps") and not args.no_accuracy and args.precision != "fp64":
+        out["accuracy"] = accuracy_leg(args, eng, W, flux, D, qn)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample_bond = L // 2 - 1
         sample = oracle_sample(mpo, qn, mps, sample_bond)

@@ -102,6 +102,11 @@ typedef struct {
                                measurements) run FP64-accurate on the bf16 tensor cores
                                (dmrg_gemm64 mode 1); batches outside its K limit stay on the
                                FP64 units.  0 = FP64 units throughout.                          */
+    int svd_plain_jacobi;   /* 1 = every split's one-sided Jacobi runs on the sector matrix W
+                               itself; 0 (default) = on R^T from a Householder QR W = QR (a
+                               few sweeps instead of many; sectors taller than the QR panel's
+                               shared-memory limit, about 1700 rows, fall back to the plain
+                               Jacobi)                                                          */
 } dmrg_config;
 
 typedef struct {
@@ -207,11 +212,15 @@ dmrg_status dmrg_get_lambda(dmrg_ctx* ctx, int b, double* lam_out, int cap, int*
  * Region mode or mixed precision: DMRG_ERR_STATE. */
 dmrg_status dmrg_energy_gradient(dmrg_ctx* ctx, double* Wbar, double* E_out);
 
-/* Site tensor j of the serial state (checkpointing): the packed layout of dmrg_set_mps for
- * bonds (j, j + 1) as dmrg_get_bond reports them, copied to host memory out[cap] (FP64, caller
- * owned); *n_out = its element count (DMRG_ERR_CAPACITY, with *n_out set, if cap is smaller).
- * Together with dmrg_get_bond and dmrg_get_center this reproduces the state through
- * dmrg_set_mps.  Region mode: DMRG_ERR_STATE.  Synchronises the stream. */
+/* Site tensor j of the state (checkpointing): the packed layout of dmrg_set_mps for bonds
+ * (j, j + 1) as dmrg_get_bond reports them, copied to host memory out[cap] (FP64, caller owned);
+ * *n_out = its element count (DMRG_ERR_CAPACITY, with *n_out set, if cap is smaller).  Serial
+ * mode: together with dmrg_get_bond and dmrg_get_center this reproduces the state through
+ * dmrg_set_mps (canonical = 1).  Region mode: site j of the region holding it, except that the
+ * first site of every region right of a boundary b carries V_b = Lambda_b^-1 on its left bond, so
+ * the exported sites contract to the real-space parallel state, the regions joined by V at every
+ * boundary as in Eq. (merge); that MPS is not canonical (load it with canonical = 0).
+ * Synchronises the stream. */
 dmrg_status dmrg_get_site(dmrg_ctx* ctx, int j, double* out, long long cap, long long* n_out);
 
 /* Inverse canonical gauge of the serial state (Sec. IV, Figs. 8 and 9): a copy of the state,
@@ -376,7 +385,9 @@ dmrg_status dmrg_env_right(const dmrg_bond_desc* bd, int prec, const double* Rin
  * normalised to sum lambda^2 = 1.  `accurate` selects the mode: 0 FP64 one-sided Jacobi; 1 the
  * same with the Appendix recursion (eps 1e-4); 2 the mixed-precision engine's split: FP32 block
  * Jacobi, cutoff raised to 1e-5 lambda_max (above the FP32 rounding level), A re-orthonormalised
- * in FP64 (Newton-Schulz), B = V^T as computed in FP32.  Other values: DMRG_ERR_ARG.
+ * in FP64 (Newton-Schulz), B = V^T as computed in FP32.  Adding 4 to the mode runs the Jacobi
+ * on the sector matrices themselves instead of on R^T from their Householder QR (the default
+ * for modes 0-2).  Other values: DMRG_ERR_ARG.
  * Outputs: middle-bond sectors (nm_out, qm_out[cap], mm_out[cap]), A_dev/B_dev/lam_dev sized
  * by the caller for the worst case (no truncation), trunc_out (nullable) the discarded weight.
  * Synchronises the stream (the kept sector sizes are returned to the host). */

@@ -53,7 +53,7 @@ class Profile(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p), ("svd_fp64", C.c_int),
-                ("fp64_emulation", C.c_int)]
+                ("fp64_emulation", C.c_int), ("svd_plain_jacobi", C.c_int)]
 
 
 class SweepParams(C.Structure):
@@ -247,7 +247,8 @@ def env_right(bond: Bond, prec, Rin_dev, B_dev, Rout_dev, stream=0):
 
 def svd_split(bond: Bond, psi_dev, m_max, accurate, A_dev, lam_dev, B_dev, cap=4096, stream=0):
     """Returns (middle-bond sectors dict, discarded weight).  accurate: False/0 FP64 Jacobi,
-    True/1 with the accurate recursion, 2 the FP32 block-Jacobi split of the mixed-precision engine."""
+    True/1 with the accurate recursion, 2 the FP32 block-Jacobi split of the mixed-precision engine;
+    + 4: the Jacobi on the sector matrices themselves (no QR preconditioning)."""
     nm = C.c_int(0)
     qm = np.zeros(cap, np.int32)
     mm = np.zeros(cap, np.int32)
@@ -281,7 +282,7 @@ class Engine:
     """A DMRG state on the GPU: MPO, MPS, environments, optional real-space regions."""
 
     def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0, svd_fp64=False,
-                 fp64_emulation=False):
+                 fp64_emulation=False, svd_plain_jacobi=False):
         self._keep = [_f64(W), _i32(flux), _i32(D), _i32(qn)]
         W_, f_, D_, q_ = self._keep
         self.L = len(D_) - 1
@@ -289,7 +290,8 @@ class Engine:
         self._wshapes = [(int(D_[j]), len(q_), len(q_), int(D_[j + 1])) for j in range(self.L)]
         desc = MpoDesc(self.L, len(q_), _ptr(q_, _ip), _ptr(D_, _ip), _ptr(f_, _ip), _ptr(W_, _dp), int(qtot))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)), int(bool(fp64_emulation)))
+        cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)), int(bool(fp64_emulation)),
+                     int(bool(svd_plain_jacobi)))
         h = C.c_void_p()
         _check(lib().dmrg_init_mpo(C.byref(h), C.byref(desc), C.byref(cfg)))
         self._h = h
@@ -419,6 +421,13 @@ class Engine:
         bonds = [self.bond(b) for b in range(self.L + 1)]
         data = np.concatenate([self.site(j) for j in range(self.L)])
         return bonds, data, self.center()
+
+    def region_state(self):
+        """(bonds, packed site data) of the real-space parallel state (every boundary's V in the
+        first site to its right); not canonical: load it with set_mps(bonds, data)."""
+        bonds = [self.bond(b) for b in range(self.L + 1)]
+        data = np.concatenate([self.site(j) for j in range(self.L)])
+        return bonds, data
 
     def center(self, region=0):
         s = C.c_int(0)

@@ -176,10 +176,20 @@ dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int 
         cudaStream_t st = (cudaStream_t)stream;
         std::vector<int> qn(bd->qn_local, bd->qn_local + bd->d);
         Sec bl = make_sec(bd->nl, bd->ql, bd->ml), br = make_sec(bd->nr, bd->qr, bd->mr);
-        PD_REQUIRE(accurate >= 0 && accurate <= 2, DMRG_ERR_ARG, "mode must be 0, 1 or 2");
+        PD_REQUIRE(accurate >= 0 && accurate <= 6 && accurate != 3, DMRG_ERR_ARG, "mode must be 0-2, or 4-6");
+        const int plain = accurate >= 4;
+        accurate &= 3;
         const bool fp32 = accurate == 2;
-        SplitResult r = svd_split(bl, br, qn, qn, psi_dev, m_max, 1e-12, accurate == 1, 0, 0, A_dev, B_dev, lam_dev, st,
-                                  fp32);
+        const int saved_qr = g_svd_qr;
+        g_svd_qr = plain ? 0 : 1;
+        SplitResult r;
+        try {
+            r = svd_split(bl, br, qn, qn, psi_dev, m_max, 1e-12, accurate == 1, 0, 0, A_dev, B_dev, lam_dev, st, fp32);
+        } catch (...) {
+            g_svd_qr = saved_qr;
+            throw;
+        }
+        g_svd_qr = saved_qr;
         if (fp32) orthonormalize_factor(bl, r.mid, qn, A_dev, true, st);
         PD_REQUIRE(r.mid.n() <= cap, DMRG_ERR_CAPACITY, "output sector capacity too small");
         *nm_out = r.mid.n();

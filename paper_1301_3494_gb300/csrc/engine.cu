@@ -96,6 +96,7 @@ struct dmrg_ctx {
     int prec = DMRG_FP64, kmax = 8;
     bool svd_fp64 = false;       // mixed modes: FP64 splits on ordinary bonds too
     bool emu = false;            // FP64 grouped GEMMs on the bf16 tensor cores (ozaki.cu)
+    bool svd_plain = false;      // splits by the plain Jacobi on W (no QR preconditioning)
     cudaStream_t base = nullptr;
     std::unique_ptr<Chain> serial;
     std::vector<std::unique_ptr<Chain>> reg;
@@ -351,13 +352,14 @@ void parallel_items(const std::vector<int>& items, F fn, bool serial = false) {
     PD_CK(cudaGetDevice(&dev));
     PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int cap = items.size() > 1 ? std::max(1, sms / (int)items.size()) : 0;
-    const int emu = g_gemm64_emu;
+    const int emu = g_gemm64_emu, qr = g_svd_qr;
     for (size_t t = 0; t < items.size(); ++t)
         th.emplace_back([&, t]() {
             try {
                 PD_CK(cudaSetDevice(dev));
                 g_sm_cap = cap;
                 g_gemm64_emu = emu;
+                g_svd_qr = qr;
                 fn(items[t]);
             } catch (const Error& e) {
                 errs[t] = e;
@@ -625,9 +627,15 @@ StepStats region_sweep(dmrg_ctx* c, const dmrg_sweep_params* p) {
 // ------------------------------------------------------------------------------------------
 // The context's FP64-GEMM choice holds on the calling thread for the duration of the call.
 struct EmuGuard {
-    int saved;
-    explicit EmuGuard(const dmrg_ctx* c) : saved(g_gemm64_emu) { g_gemm64_emu = (c && c->emu) ? 1 : 0; }
-    ~EmuGuard() { g_gemm64_emu = saved; }
+    int saved, saved_qr;
+    explicit EmuGuard(const dmrg_ctx* c) : saved(g_gemm64_emu), saved_qr(g_svd_qr) {
+        g_gemm64_emu = (c && c->emu) ? 1 : 0;
+        g_svd_qr = (c && c->svd_plain) ? 0 : 1;
+    }
+    ~EmuGuard() {
+        g_gemm64_emu = saved;
+        g_svd_qr = saved_qr;
+    }
 };
 #define CTX_TRY try { EmuGuard emu_guard_(c);
 #define CTX_CATCH(ctx)                                        \
@@ -686,6 +694,7 @@ dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_c
     C->kmax = cfg->kmax > 0 ? cfg->kmax : 8;
     C->svd_fp64 = cfg->svd_fp64 != 0;
     C->emu = cfg->fp64_emulation != 0;
+    C->svd_plain = cfg->svd_plain_jacobi != 0;
     PD_REQUIRE(!C->emu || tc_available(), DMRG_ERR_STATE, "FP64 emulation needs sm_103 tensor cores");
     PD_REQUIRE(C->kmax >= 2 && C->kmax <= 32, DMRG_ERR_ARG, "kmax must be in [2, 32]");
     C->base = (cudaStream_t)cfg->stream;
@@ -948,13 +957,32 @@ dmrg_status dmrg_energy_gradient(dmrg_ctx* c, double* Wbar, double* E) {
 dmrg_status dmrg_get_site(dmrg_ctx* c, int j, double* out, long long cap, long long* n) {
     CTX_TRY
     PD_REQUIRE(c && n && c->have_state && j >= 0 && j < c->L, DMRG_ERR_ARG, "bad argument");
-    PD_REQUIRE(c->reg.empty(), DMRG_ERR_STATE, "site export needs a serial state");
-    Chain& ch = *c->serial;
-    const SiteLayout S = site_layout(ch.bond[j], ch.bond[j + 1], c->qn);
+    Chain* ch = c->serial.get();
+    int k = 0;
+    if (!c->reg.empty()) {
+        for (k = 0; k < (int)c->reg.size(); ++k)
+            if (j >= c->reg[k]->p && j <= c->reg[k]->q) break;
+        PD_REQUIRE(k < (int)c->reg.size(), DMRG_ERR_STATE, "site outside every region");
+        ch = c->reg[k].get();
+    }
+    const SiteLayout S = site_layout(ch->bond[j], ch->bond[j + 1], c->qn);
     *n = S.size;
     PD_REQUIRE(S.size <= cap && out, DMRG_ERR_CAPACITY, "capacity too small");
-    if (S.size) PD_CK(cudaMemcpyAsync(out, ch.site[j].p, S.size * 8, cudaMemcpyDeviceToHost, ch.st));
-    PD_CK(cudaStreamSynchronize(ch.st));
+    cudaStream_t st = ch->st;
+    if (S.size && k > 0 && j == ch->p) {
+        // first site of a region right of a boundary b = j: V_b = Lambda_b^-1 absorbed into its
+        // rows, so the exported sites contract to ... psi_3 V psi_4 ... (Eq. merge)
+        DBuf Vd, tmp;
+        upload(Vd, c->V.at(j), st);
+        tmp.ensure(S.size * 8, st);
+        scale_site(ch->bond[j], ch->bond[j + 1], c->qn, ch->site[j].as<double>(), Vd.as<double>(), false,
+                   tmp.as<double>(), st);
+        PD_CK(cudaMemcpyAsync(out, tmp.p, S.size * 8, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+    } else {
+        if (S.size) PD_CK(cudaMemcpyAsync(out, ch->site[j].p, S.size * 8, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+    }
     return DMRG_OK;
     CTX_CATCH(c)
 }

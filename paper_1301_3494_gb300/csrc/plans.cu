@@ -8,6 +8,8 @@
 
 namespace pd {
 
+thread_local int g_svd_qr = 1;
+
 // ------------------------------------------------------------------------------------------
 // Layouts
 // ------------------------------------------------------------------------------------------
@@ -1319,12 +1321,42 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         PD_CK(cudaEventCreate(&sv1));
         PD_CK(cudaEventRecord(sv0, st));
     }
+    // QR preconditioning: the Jacobi runs on X = R^T (n x n per sector, stored at v_off of dV) with
+    // its rotations accumulated in dVJ; afterwards dW receives Q [V_J Sigma; 0] and dV the right
+    // singular vectors -- the same outputs as the plain Jacobi on W.
+    QrPlan qp;
+    DBuf dxsecs, dVJ;
+    std::vector<SvdSec> xs;
+    if (g_svd_qr && woff > 0) {
+        if (fp32) qp.build<float>(ss, st);
+        else qp.build<double>(ss, st);
+        if (qp.ok) {
+            xs = ss;
+            for (auto& x : xs) {
+                x.w_off = x.v_off;
+                x.p = x.n;
+            }
+            upload(dxsecs, xs, st);
+            dVJ.ensure(std::max<long long>(1, voff) * es, st);
+        }
+    }
+    const bool use_qr = qp.ok && !xs.empty();
+    const SvdSec* jsecs = use_qr ? dxsecs.as<SvdSec>() : dsecs.as<SvdSec>();
+    const int jmaxp = use_qr ? maxn : maxp;
     if (fp32) {
         run_copy<double>(gather, psi, dW.p, Num::F32, st);
-        launch_svd_init_v<float>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<float>(), st);
+        float* JW = dW.as<float>();
+        float* JV = dV.as<float>();
+        if (use_qr) {
+            qp.factor<float>(dW.as<float>(), st);
+            qp.form_rt<float>(dW.as<float>(), dV.as<float>(), st);
+            JW = dV.as<float>();
+            JV = dVJ.as<float>();
+        }
+        launch_svd_init_v<float>(jsecs, nsec, maxn, JV, st);
         // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it; the
         // kept factor that joins a block is re-orthonormalised in FP64 afterwards
-        const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)maxp));
+        const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)jmaxp));
         // block Jacobi: one task per block pair, n / 16 - 1 rounds per sweep
         std::vector<BjSec> bs(nsec);
         std::vector<int> task_sec;
@@ -1345,9 +1377,15 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         dgmax.ensure(std::max(1, nsec) * 4, st);
         PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
         PD_CK(cudaMemsetAsync(dflops.p, 0, 8, st));
-        launch_bjacobi(dsecs.as<SvdSec>(), dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, maxp, maxn, 40,
-                       2, dW.as<float>(), dV.as<float>(), tol, 8.0f * FLT_EPSILON, dgmax.as<float>(), drot.as<int>(),
-                       drot.as<int>() + max_sweeps, bar, jerr, dflops.as<unsigned long long>(), st);
+        launch_bjacobi(jsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, jmaxp, maxn, 40, 2, JW,
+                       JV, tol, 8.0f * FLT_EPSILON, dgmax.as<float>(), drot.as<int>(), drot.as<int>() + max_sweeps, bar,
+                       jerr, dflops.as<unsigned long long>(), st);
+        if (use_qr) {
+            DBuf dWo;
+            dWo.ensure(std::max<long long>(1, woff) * es, st);
+            qp.finish<float>(dW.as<float>(), dV.as<float>(), dVJ.as<float>(), dWo.as<float>(), st);
+            dW = std::move(dWo);
+        }
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
         run_copy<double>(gather, psi, dW.p, Num::F64, st);
@@ -1356,11 +1394,24 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
             dM.ensure(woff * 8, st);
             PD_CK(cudaMemcpyAsync(dM.p, dW.p, woff * 8, cudaMemcpyDeviceToDevice, st));
         }
-        launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
-        const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
-        launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps,
-                              dW.as<double>(), dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(),
-                              drot.as<int>() + max_sweeps, bar, jerr, st);
+        double* JW = dW.as<double>();
+        double* JV = dV.as<double>();
+        if (use_qr) {
+            qp.factor<double>(dW.as<double>(), st);
+            qp.form_rt<double>(dW.as<double>(), dV.as<double>(), st);
+            JW = dV.as<double>();
+            JV = dVJ.as<double>();
+        }
+        launch_svd_init_v<double>(jsecs, nsec, maxn, JV, st);
+        const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)jmaxp);
+        launch_jacobi<double>(jsecs, nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps, JW, JV, tol, 0.0, nullptr,
+                              drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr, st);
+        if (use_qr) {
+            DBuf dWo;
+            dWo.ensure(std::max<long long>(1, woff) * es, st);
+            qp.finish<double>(dW.as<double>(), dV.as<double>(), dVJ.as<double>(), dWo.as<double>(), st);
+            dW = std::move(dWo);
+        }
         launch_svd_finish<double>(dsecs.as<SvdSec>(), nsec, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
         if (accurate && woff > 0)
             accurate_refine(ss, dsecs.as<SvdSec>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(),

@@ -340,6 +340,34 @@ void orthonormalize_factor(const Sec& bl, const Sec& br, const std::vector<int>&
 void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
                       long long* a_elems, long long* b_elems, long long* lam_elems);
 
+// Householder QR preconditioning of the one-sided Jacobi SVD (qr.cu).  Per sector: W (p x n,
+// column-major at w_off, n <= p) and npanel T factors at t_off.
+struct QrSec {
+    long long w_off, t_off;
+    int p, n;
+};
+// Largest sector row count whose QR panel fits in shared memory.
+int qr_max_rows(bool f64);
+struct QrPlan {
+    std::vector<QrSec> secs;
+    std::vector<int> act_off, trail_off, all_off;
+    DBuf dsecs, dact, dtrail, dall, dcols, dxoff, dT;
+    int npanel = 0, ncols = 0, max_rows = 0;
+    bool ok = false;                  // false: a sector is too tall (use the plain Jacobi)
+    // Lists for the sectors ss (w_off, p, n; v_off = offset of the n x n matrices X, V_J, Y).
+    template <class T> void build(const std::vector<SvdSec>& ss, cudaStream_t st);
+    // W <- R (on and above the diagonal) and the Householder vectors (below it).
+    template <class T> void factor(T* W, cudaStream_t st);
+    // X = R^T (n x n per sector at v_off).
+    template <class T> void form_rt(const T* W, T* X, cudaStream_t st);
+    // After the Jacobi on X (X V_J = Y): Y <- Y Sigma^-1 (the right singular vectors of W), Wout <-
+    // Q [V_J Sigma; 0] (left singular vectors times Sigma), with the reflectors in W.
+    template <class T> void finish(const T* W, T* Y, const T* VJ, T* Wout, cudaStream_t st);
+};
+// QR preconditioning of the split's Jacobi SVDs (on by default; the plain Jacobi when 0), set on
+// the calling thread.
+extern thread_local int g_svd_qr;
+
 // Davidson on the projected Hamiltonian (FP64 vectors).
 struct DavResult {
     double theta = 0.0, rnorm = 0.0;

@@ -90,8 +90,11 @@ def test_env_updates_fp64_match_oracle(kind, m):
         assert np.abs(gotR[k] - r).max() <= 1e-12 * scale, k
 
 
+@pytest.mark.parametrize("plain", [0, 4])
 @pytest.mark.parametrize("kind,m,mmax", [("chain", 60, 1000), ("chain", 200, 120), ("cyl", 160, 90), ("tfim", 80, 50)])
-def test_svd_split_matches_oracle(kind, m, mmax):
+def test_svd_split_matches_oracle(kind, m, mmax, plain):
+    """FP64 split (Jacobi on R^T from a Householder QR, or with plain = 4 on the sector matrices)
+    against the oracle: block table, discarded weight, singular values, factors."""
     mpo, qn, bl, br, _, j, rng = _bond_case(kind, m, 3)
     # a wavefunction with a decaying spectrum (like a ground state)
     psi = {}
@@ -105,7 +108,7 @@ def test_svd_split_matches_oracle(kind, m, mmax):
     Ad = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
     Bd = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
     ld = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
-    mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, False, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
+    mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, plain, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
     torch.cuda.synchronize()
     assert mid == counts                                   # block table bit-exact
     assert abs(tr - err) <= 1e-12 + 1e-9 * err
@@ -125,8 +128,9 @@ def test_svd_split_matches_oracle(kind, m, mmax):
         assert np.abs(rec_g[k] - rec_o[k]).max() <= 1e-11, k
 
 
+@pytest.mark.parametrize("plain", [0, 4])
 @pytest.mark.parametrize("kind,m,seed", [("chain", 60, 7), ("cyl", 120, 8)])
-def test_svd_split_accurate_graded(kind, m, seed):
+def test_svd_split_accurate_graded(kind, m, seed, plain):
     """Appendix accurate SVD (mode 1) on graded blocks D1 G D2 (rows graded over 7 decades,
     columns over 2): every singular value agrees with the oracle's accurate SVD to 1e-9 relative
     (the oracle's recursion is pinned against 60-digit arithmetic), the block table exactly, and
@@ -145,7 +149,7 @@ def test_svd_split_accurate_graded(kind, m, seed):
     Ad = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
     Bd = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
     ld = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
-    mid, tr = pd.svd_split(bond, x.data_ptr(), 10 ** 9, 1, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
+    mid, tr = pd.svd_split(bond, x.data_ptr(), 10 ** 9, 1 + plain, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
     torch.cuda.synchronize()
     assert mid == counts
     lam_ref = np.concatenate([lam[q] for q in sorted(lam)])
@@ -164,9 +168,10 @@ def test_svd_split_accurate_graded(kind, m, seed):
         assert np.abs(rec_g[k] - rec_o[k]).max() <= 1e-12 * lam_ref.max(), k
 
 
+@pytest.mark.parametrize("plain", [0, 4])
 @pytest.mark.parametrize("kind,m,mmax", [("chain", 200, 120), ("cyl", 160, 90), ("cyl", 420, 300), ("tfim", 80, 50),
                                           ("chain", 3200, 2000)])
-def test_svd_split_fp32_block_jacobi(kind, m, mmax):
+def test_svd_split_fp32_block_jacobi(kind, m, mmax, plain):
     """Mixed-precision split (FP32 block Jacobi, A re-orthonormalised in FP64) against the FP64
     oracle.  FP32 columns carry absolute errors ~eps_f32 * lambda_max and pairs stop rotating at a
     relative off-diagonal of 3e-5, so singular values agree to 1e-4 * lambda_max and the
@@ -187,7 +192,7 @@ def test_svd_split_fp32_block_jacobi(kind, m, mmax):
     Ad = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
     Bd = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
     ld = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
-    mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, 2, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
+    mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, 2 + plain, Ad.data_ptr(), ld.data_ptr(), Bd.data_ptr())
     torch.cuda.synchronize()
     # the oracle's full spectrum decides whether the cut is resolvable in FP32
     full = O.split_two_site(psi, bl, br, qn, 10 ** 9)[1]

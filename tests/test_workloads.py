@@ -35,7 +35,7 @@ def test_snake_order_is_a_permutation():
     assert idx == list(range(Lx * Ly))
 
 
-@pytest.mark.parametrize("name", ["heis", "tfim", "aklt", "cyl", "tri", "jq2"])
+@pytest.mark.parametrize("name", ["heis", "tfim", "aklt", "cyl", "tri", "jq2", "field"])
 def test_mpo_equals_operator_sum(name):
     """The FSM MPO contracted to a matrix equals the Kronecker-product Hamiltonian."""
     if name == "heis":
@@ -48,6 +48,10 @@ def test_mpo_equals_operator_sum(name):
         L = 8; site = wl.spin_half(); terms = wl.heisenberg_terms(wl.square_cylinder_bonds(2, 4))
     elif name == "tri":
         L = 9; site = wl.spin_half(); terms = wl.heisenberg_terms(wl.triangular_cylinder_bonds(3, 3))
+    elif name == "field":
+        L = 8; site = wl.spin_half()
+        terms = (wl.heisenberg_terms(wl.square_cylinder_bonds(2, 4))
+                 + wl.field_terms(np.random.default_rng(4).uniform(-0.5, 0.5, L)))
     else:
         L = 8
         site = wl.spin_half()

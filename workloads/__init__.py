@@ -165,6 +165,11 @@ def heisenberg_terms(bonds, J=1.0):
     return terms
 
 
+def field_terms(hz):
+    """H = sum_i hz_i S^z_i."""
+    return [_string(float(h), (i, "Sz")) for i, h in enumerate(hz)]
+
+
 def tfim_terms(L, J=1.0, h=1.0):
     """H = -J sum sigma^z_i sigma^z_{i+1} - h sum sigma^x_i (open chain)."""
     terms = [_string(-J, (i, "Z"), (i + 1, "Z")) for i in range(L - 1)]
@@ -361,6 +366,16 @@ def heisenberg_chain(L, J=1.0, spin="half"):
 
 def heisenberg_square_cylinder(Lx, Ly, J=1.0):
     return build_mpo(Lx * Ly, spin_half(), heisenberg_terms(square_cylinder_bonds(Lx, Ly), J))
+
+
+def field_square_cylinder(Lx, Ly, seed, width=0.5, J=1.0):
+    """Heisenberg square cylinder plus a random longitudinal field sum_i h_i S^z_i, h_i i.i.d.
+    U[-width, width] from default_rng(seed): S^z_tot is still conserved (U(1)), but neither the
+    SU(2) multiplets nor the spin-flip pairs of Schmidt values are degenerate any more, so a
+    truncation cut has no symmetry-enforced ties."""
+    h = np.random.default_rng(seed).uniform(-width, width, Lx * Ly)
+    terms = heisenberg_terms(square_cylinder_bonds(Lx, Ly), J) + field_terms(h)
+    return build_mpo(Lx * Ly, spin_half(), terms)
 
 
 def heisenberg_triangular_cylinder(Lx, Ly, J=1.0):
