@@ -61,8 +61,20 @@ def parse():
                          "accuracy: the same serial sweeps (m ramped to --acc-m) in FP64 and in --precision "
                          "mode from the same seeded state, energies and sweep times compared")
     ap.add_argument("--acc-m", type=int, default=500)
+    ap.add_argument("--acc-tol", type=float, default=1e-8,
+                    help="accuracy leg: Davidson residual tolerance of both same-state sweeps")
+    ap.add_argument("--acc-iters", type=int, default=12,
+                    help="accuracy leg: Davidson iteration cap (FP64; tensor-core iterations of the mixed sweep)")
+    ap.add_argument("--acc-refine", type=int, default=12,
+                    help="accuracy leg: FP32-accurate refinement iterations of the mixed sweep (after --dav-iters "
+                         "tensor-core iterations)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="sweeps mode: skip the FP64 evaluation and the FP64-vs-mixed same-state sweeps")
+    ap.add_argument("--env-fp64", action="store_true",
+                    help="mixed modes: FP64-accurate environments (default: FP32)")
+    ap.add_argument("--edges", type=int, default=2, choices=[0, 1, 2],
+                    help="mixed modes: FP64 solves next to the region boundaries and in the merges (1: Davidson, "
+                         "2: Davidson and split; 0: mixed precision everywhere)")
     ap.add_argument("--svd-plain-jacobi", action="store_true",
                     help="splits by the one-sided Jacobi on the sector matrices (no QR preconditioning)")
     ap.add_argument("--fp64-emulation", action="store_true",
@@ -76,7 +88,10 @@ def parse():
     ap.add_argument("--chain-spin", choices=["half", "one"], default="half")
     ap.add_argument("--chain-warmup", type=int, default=0)
     ap.add_argument("--chain-runs", default="",
-                    help="chain: runs to make, comma-separated precision[:svd64] (default: fp64 and --precision)")
+                    help="chain: runs to make, comma-separated precision[:svd64][:rN refinement iterations]"
+                         "[:e64 FP64-accurate environments][:edge FP64 solves next to the boundaries][:edge2 and FP64 splits there]"
+                         "[:dN Davidson iterations][:tz fixed iteration count]"
+                         " (default: fp64 and --precision)")
     ap.add_argument("--grad-m", type=int, default=128)
     ap.add_argument("--grad-jq-m", type=int, default=128)
     ap.add_argument("--acc-sweeps", type=int, default=6)
@@ -370,11 +385,18 @@ def chain_mode(args):
     finals = {}
     runs = [r for r in args.chain_runs.split(",") if r] or ["fp64", args.precision]
     for run in runs:
-        prec = run.split(":")[0]
-        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax, svd_fp64=run.endswith(":svd64"),
-                        fp64_emulation=args.fp64_emulation and prec == "fp64")
+        opts = run.split(":")
+        prec = opts[0]
+        e64 = "e64" in opts
+        edges = 2 if "edge2" in opts else (1 if "edge" in opts else 0)
+        eng = pd.Engine(W, flux, D, qn, 0, prec, args.kmax, svd_fp64="svd64" in opts,
+                        fp64_emulation=(args.fp64_emulation and prec == "fp64") or e64 or edges > 0, env_fp64=e64,
+                        accurate_edges=edges)
         eng.set_mps(mps.bonds, data)
-        dav = dict(dav_tol=1e-9, dav_max_iter=12, refine_iters=0 if prec == "fp64" else 6, serial_regions=1)
+        refine = next((int(o[1:]) for o in opts[1:] if o.startswith("r") and o[1:].isdigit()), 6)
+        dav_it = next((int(o[1:]) for o in opts[1:] if o.startswith("d") and o[1:].isdigit()), 12)
+        dav = dict(dav_tol=0.0 if "tz" in opts else 1e-9, dav_max_iter=dav_it,
+                   refine_iters=0 if prec == "fp64" else refine, serial_regions=1)
         t0 = time.perf_counter()
         eng.setup_regions(args.regions, args.chain_warmup, ramp[0], **dav)
         t_setup = time.perf_counter() - t0
@@ -401,9 +423,9 @@ def accuracy_leg(args, eng, W, flux, D, qn):
     """The accuracy half of the metric, after the timed sweeps: (1) the timed engine's state,
     exported as one MPS (the regions joined by V = Lambda^-1 at every boundary, Eq. (merge)), is
     canonicalised and evaluated by an FP64 engine; (2) from that canonical state, one FP64 serial
-    sweep and one mixed-precision serial sweep (same m, same Davidson iteration count: the mixed
-    sweep's tensor-core iterations plus its FP32 refinement), both timed; the mixed result is
-    evaluated by an FP64 engine.  Returns the record for the JSON line."""
+    sweep and one mixed-precision serial sweep (same m; Davidson to the same residual tolerance:
+    FP64 iterations, or tensor-core iterations followed by FP32-accurate refinement), both
+    timed; the mixed result is evaluated by an FP64 engine.  Returns the record for the JSON line."""
     import torch
     import paper_1301_3494_gb300 as pd
     emu = True      # FP64 GEMMs of the FP64 engines on the tensor cores (FP64-accurate)
@@ -412,24 +434,25 @@ def accuracy_leg(args, eng, W, flux, D, qn):
         bonds, data = eng.region_state()
     else:
         bonds, data, _ = eng.state()
+    eng.close()                                  # its device memory goes back for the engines below
     f64 = pd.Engine(W, flux, D, qn, 0, "fp64", args.kmax, fp64_emulation=emu)
     f64.set_mps(bonds, data)                     # canonicalised by the engine (FP64 SVDs)
     e_state = f64.energy()
     b0, d0, c0 = f64.state()
     t_canon = time.perf_counter() - t0
-    iters = args.dav_iters + args.refine_iters
     torch.cuda.synchronize()
     t = time.perf_counter()
-    f64.sweep(args.m, dav_tol=0.0, dav_max_iter=iters, refine_iters=0)
+    g64 = f64.sweep(args.m, dav_tol=args.acc_tol, dav_max_iter=args.acc_iters, refine_iters=0)
     torch.cuda.synchronize()
     fp64_s = time.perf_counter() - t
     e_fp64 = f64.energy()
     f64.close()
-    mx = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax)
+    env64 = args.env_fp64
+    mx = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax, fp64_emulation=True, env_fp64=env64)
     mx.set_mps(b0, d0, center=c0)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    mx.sweep(args.m, dav_tol=0.0, dav_max_iter=args.dav_iters, refine_iters=args.refine_iters)
+    gmx = mx.sweep(args.m, dav_tol=args.acc_tol, dav_max_iter=args.dav_iters, refine_iters=args.acc_refine)
     torch.cuda.synchronize()
     mixed_s = time.perf_counter() - t
     b1, d1, c1 = mx.state()
@@ -445,7 +468,10 @@ def accuracy_leg(args, eng, W, flux, D, qn):
             "E_start": e_state, "E_fp64": e_fp64, "E_mixed_fp64_eval": e_mixed, "E_mixed_own_environments": e_mixed_own,
             "dE_over_E": abs(e_mixed - e_fp64) / abs(e_fp64), "fp64_sweep_s": fp64_s, "mixed_sweep_s": mixed_s,
             "speedup": fp64_s / mixed_s, "schedule": "serial sweep (L - 1 steps right, L - 1 left), both precisions",
-            "davidson": f"FP64: {iters} iterations; mixed: {args.dav_iters} tensor-core + {args.refine_iters} FP32-accurate",
+            "davidson": (f"residual <= {args.acc_tol:g} max(1, |E|); FP64: <= {args.acc_iters} iterations; mixed: <= "
+                         f"{args.dav_iters} tensor-core + <= {args.acc_refine} FP32-accurate iterations"),
+            "dav_nonconverged": {"fp64": g64["dav_nonconv"], "mixed": gmx["dav_nonconv"]},
+            "max_trunc_err": {"fp64": g64["max_trunc_err"], "mixed": gmx["max_trunc_err"]},
             "fp64_gemm": "emulated on bf16 tensor cores (FP64-accurate)" if emu else "FP64 units"},
         "canonicalise_and_evaluate_s": t_canon,
     }
@@ -682,8 +708,12 @@ def main():
         chain_mode(args)
         return
     W, flux, D = wl.pack_mpo(mpo)
-    eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax, fp64_emulation=args.fp64_emulation,
-                    svd_plain_jacobi=args.svd_plain_jacobi)
+    mixed = args.precision != "fp64"
+    env64 = mixed and args.env_fp64
+    edges = args.edges if mixed else 0
+    emu = args.fp64_emulation or env64 or edges > 0
+    eng = pd.Engine(W, flux, D, qn, 0, args.precision, args.kmax, fp64_emulation=emu,
+                    svd_plain_jacobi=args.svd_plain_jacobi, env_fp64=env64, accurate_edges=edges)
     data = np.concatenate([wl.pack_site(mps.sites[j], mps.bonds[j], mps.bonds[j + 1], qn) for j in range(L)])
     t_setup = time.perf_counter()
     eng.set_mps(mps.bonds, data, center=center)
@@ -784,7 +814,10 @@ def main():
                    "region_schedule": (("concurrent" if args.concurrent_regions else "serial")
                                        if args.mode == "sweeps" else None),
                    "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
-                   "fp64_gemm": "emulated on bf16 tensor cores" if args.fp64_emulation else "FP64 units",
+                   "fp64_gemm": "emulated on bf16 tensor cores" if emu else "FP64 units",
+                   "environments": "FP64" if (env64 or not mixed) else "FP32",
+                   "boundary_solves": {0: "mixed precision", 1: "FP64 Davidson next to region boundaries and in merges",
+                                       2: "FP64 Davidson and split next to region boundaries and in merges"}[edges],
                    "svd": "one-sided Jacobi on W" if args.svd_plain_jacobi else "one-sided Jacobi on R^T (Householder QR)",
                    "setup_s": t_setup},
         "sweep_s": ms_step / 1e3 if args.mode == "sweeps" else ms_step * 2 * (L - 1) / 1e3,
@@ -808,7 +841,8 @@ def main():
                 "fp64_calls": prof["svd_fp64_calls"], "fp64_ms": prof["svd_fp64_ms"],
                 "max_sector_rows": prof["svd_max_rows"], "fp64_fallbacks": prof["svd_fp64_fallbacks"],
                 "rotated_pairs_per_sweep": [h for h in prof["svd_rot_hist"] if h > 0]},
-        "env_update_ms_per_step": prof["f32_gemm_ms"] / args.steps if args.precision != "fp64" else None,
+        "env_update_ms_per_step": ((prof["env_gemm_ms"] if env64 else prof["f32_gemm_ms"]) / args.steps
+                                   if args.precision != "fp64" else None),
         "gpu_launches": prof["launches"],
         "clocks": clocks,
     }

@@ -107,6 +107,19 @@ typedef struct {
                                few sweeps instead of many; sectors taller than the QR panel's
                                shared-memory limit, about 1700 rows, fall back to the plain
                                Jacobi)                                                          */
+    int env_fp64;           /* mixed modes: 1 = environments stored and updated FP64-accurately
+                               (FP64 GEMMs, on the tensor cores when fp64_emulation = 1; the
+                               matvec reads bf16 / FP32 copies), so their rounding does not
+                               compound from site to site; 0 (default) = FP32 storage and FP32
+                               updates.  FP64 mode: no effect.                                  */
+    int accurate_edges;     /* mixed modes: 1 = the region steps on the bonds next to a boundary
+                               (those that produce and consume the edge tensors psi_3, psi_4 of
+                               Eq. (merge)) and the merges themselves run Davidson in FP64 (FP64
+                               matvec on FP64 copies of the environments, to a 1e-10 relative
+                               residual, at most max(12, dav_max_iter + refine_iters)
+                               iterations; counted as refinement matvecs); 2 = the same and FP64
+                               splits at those steps; 0 (default) = the mixed-precision solve
+                               everywhere.                                                     */
 } dmrg_config;
 
 typedef struct {
@@ -281,7 +294,8 @@ typedef struct {
     long long mv_gemm_launches;  /* tensor-core GEMM launches of H_eff matvecs                  */
     double mv_gemm_ms;           /* their summed device time                                    */
     double mv_gemm_flops;        /* their algorithmic flops                                     */
-    long long env_gemm_launches; /* tensor-core GEMM launches of environment updates            */
+    long long env_gemm_launches; /* GEMM batches of environment updates: tensor core, and FP64
+                                    (emulated or FP64 units) with FP64-accurate environments   */
     double env_gemm_ms;
     double env_gemm_flops;
     long long f64_gemm_launches; /* FP64 grouped-GEMM launches (any use)                        */

@@ -53,7 +53,8 @@ class Profile(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("precision", C.c_int), ("kmax", C.c_int), ("stream", C.c_void_p), ("svd_fp64", C.c_int),
-                ("fp64_emulation", C.c_int), ("svd_plain_jacobi", C.c_int)]
+                ("fp64_emulation", C.c_int), ("svd_plain_jacobi", C.c_int), ("env_fp64", C.c_int),
+                ("accurate_edges", C.c_int)]
 
 
 class SweepParams(C.Structure):
@@ -282,7 +283,7 @@ class Engine:
     """A DMRG state on the GPU: MPO, MPS, environments, optional real-space regions."""
 
     def __init__(self, W, flux, D, qn, qtot=0, precision="fp64", kmax=8, stream=0, svd_fp64=False,
-                 fp64_emulation=False, svd_plain_jacobi=False):
+                 fp64_emulation=False, svd_plain_jacobi=False, env_fp64=False, accurate_edges=False):
         self._keep = [_f64(W), _i32(flux), _i32(D), _i32(qn)]
         W_, f_, D_, q_ = self._keep
         self.L = len(D_) - 1
@@ -291,7 +292,7 @@ class Engine:
         desc = MpoDesc(self.L, len(q_), _ptr(q_, _ip), _ptr(D_, _ip), _ptr(f_, _ip), _ptr(W_, _dp), int(qtot))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = Config(prec, int(kmax), C.c_void_p(stream), int(bool(svd_fp64)), int(bool(fp64_emulation)),
-                     int(bool(svd_plain_jacobi)))
+                     int(bool(svd_plain_jacobi)), int(bool(env_fp64)), int(accurate_edges))
         h = C.c_void_p()
         _check(lib().dmrg_init_mpo(C.byref(h), C.byref(desc), C.byref(cfg)))
         self._h = h

@@ -369,13 +369,19 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
         return gram_flops;
     }
     bj_inner(S, inner_sweeps, tol, noise);
-    // order the eigenvectors by decreasing eigenvalue (ties: lower index first)
+    // order the eigenvectors of the k real columns by decreasing eigenvalue (ties: lower index
+    // first); the padding columns are never rotated and keep their positions k..31 (a real
+    // column of a numerically rank-deficient pair can end with an eigenvalue rounded below zero,
+    // which must not trade places with a padding column's zero)
     if (tid < BJ_K) S.diag[tid] = S.G[tid * BJ_LD + tid];
     __syncthreads();
     if (tid < BJ_K) {
         const float d = S.diag[tid];
-        int r = 0;
-        for (int v = 0; v < BJ_K; ++v) r += (S.diag[v] > d) || (S.diag[v] == d && v < tid);
+        int r = tid;
+        if (tid < k) {
+            r = 0;
+            for (int v = 0; v < k; ++v) r += (S.diag[v] > d) || (S.diag[v] == d && v < tid);
+        }
         S.perm[r] = tid;
     }
     __syncthreads();

@@ -97,6 +97,8 @@ struct dmrg_ctx {
     bool svd_fp64 = false;       // mixed modes: FP64 splits on ordinary bonds too
     bool emu = false;            // FP64 grouped GEMMs on the bf16 tensor cores (ozaki.cu)
     bool svd_plain = false;      // splits by the plain Jacobi on W (no QR preconditioning)
+    bool env64 = false;          // mixed modes: FP64-accurate environments (PREC_ENV64)
+    int acc_edges = 0;           // mixed modes: FP64 solves next to region boundaries (2: FP64 splits there too)
     cudaStream_t base = nullptr;
     std::unique_ptr<Chain> serial;
     std::vector<std::unique_ptr<Chain>> reg;
@@ -118,12 +120,47 @@ namespace {
 
 const std::vector<int> kZero1 = {0};
 
+// Arithmetic and storage of the environments: the mixed modes keep them in FP32 unless the
+// context asks for FP64-accurate ones.
+int eprec(const dmrg_ctx* c) { return (c->env64 && c->prec != DMRG_FP64) ? PREC_ENV64 : c->prec; }
+
+// FP64 local solves (FP64 matvec on the FP64-accurate environments, Davidson to a 1e-10 residual,
+// FP64 split) for the bond steps that produce or consume a region's edge tensor next to a
+// boundary, and for the merges: the prediction Psi' = psi'_3 V psi'_4 divides the edge tensors by
+// the shared bond's singular values, so their errors must sit far below the smallest of them.
+bool fp64_solve(const dmrg_ctx* c) { return c->acc_edges > 0 && c->prec != DMRG_FP64; }
+bool fp64_edge_split(const dmrg_ctx* c) { return c->acc_edges > 1 && c->prec != DMRG_FP64; }
+
+// FP64 copy of an environment in the same layout (FP32-stored environments of the mixed modes;
+// the FP64 solve reads FP64 operands).
+const EnvSlab& env64_view(const EnvSlab& e, EnvSlab& tmp, cudaStream_t st) {
+    if (e.num == Num::F64) return e;
+    tmp.lay = e.lay;
+    tmp.num = Num::F64;
+    const long long n = std::max<long long>(1, e.lay.rows) * e.lay.ld;
+    CopyList cl;
+    const long long chunk = 1 << 20;
+    for (long long s0 = 0; s0 < n; s0 += chunk) {
+        CopyJob j{};
+        j.src = s0; j.dst = s0; j.rows = 1; j.cols = (int)std::min(chunk, n - s0);
+        j.srs = 0; j.scs = 1; j.drs = 0; j.dcs = 1; j.zero_to = 0; j.scale = 1.0;
+        cl.add(j);
+    }
+    cl.up(st);
+    tmp.buf.ensure(n * 8, st);
+    run_copy<float>(cl, e.buf.as<float>(), tmp.buf.p, Num::F64, st);
+    tmp.valid = true;
+    return tmp;
+}
+constexpr double kEdgeTol = 1e-10;
+int edge_iters(const dmrg_sweep_params* p) { return std::max(12, p->dav_max_iter + p->refine_iters); }
+
 // ------------------------------------------------------------------------------------------
 // Building blocks on a chain
 // ------------------------------------------------------------------------------------------
 void make_boundary_envs(dmrg_ctx* c, Chain& ch) {
-    env_boundary(*ch.Lenv[0], ch.bond[0], c->W[0].fl, c->prec, ch.st);
-    env_boundary(*ch.Renv[c->L], ch.bond[c->L], c->W[c->L - 1].fr, c->prec, ch.st);
+    env_boundary(*ch.Lenv[0], ch.bond[0], c->W[0].fl, eprec(c), ch.st);
+    env_boundary(*ch.Renv[c->L], ch.bond[c->L], c->W[c->L - 1].fr, eprec(c), ch.st);
 }
 
 // Untruncated right-canonicalisation with the centre on site 0 (SVDs from the right).
@@ -174,23 +211,41 @@ void right_canonicalize(dmrg_ctx* c, Chain& ch) {
 
 void build_right_envs(dmrg_ctx* c, Chain& ch, int down_to) {
     for (int j = c->L - 1; j >= down_to; --j) {
-        env_alloc(*ch.Renv[j], ch.bond[j], c->W[j].fl, c->prec, ch.st);
+        env_alloc(*ch.Renv[j], ch.bond[j], c->W[j].fl, eprec(c), ch.st);
         env_update_right(ch.bond[j], ch.bond[j + 1], c->qn, c->W[j], *ch.Renv[j + 1], ch.site[j].as<double>(),
-                         *ch.Renv[j], c->prec, ch.err.as<unsigned>(), ch.st);
+                         *ch.Renv[j], eprec(c), ch.err.as<unsigned>(), ch.st);
     }
 }
 
 // Davidson on psi at bond j (sites j, j+1) with the chain's environments L[j], R[j+2].
 DavResult solve_bond(dmrg_ctx* c, Chain& ch, int j, EnvSlab& Lj, EnvSlab& Rj, DBuf& psi, const dmrg_sweep_params* p,
-                     StepStats& s, double* flops_per_mv) {
+                     StepStats& s, double* flops_per_mv, bool edge = false) {
+    if (edge && fp64_solve(c)) {
+        EnvSlab l64, r64;
+        const EnvSlab& L = env64_view(Lj, l64, ch.st);
+        const EnvSlab& R = env64_view(Rj, r64, ch.st);
+        auto plan = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), L.lay, R.lay, DMRG_FP64, ch.st);
+        DavResult r = davidson(*plan, L, R, psi.as<double>(), c->kmax, kEdgeTol, edge_iters(p),
+                               ch.err.as<unsigned>(), ch.st);
+        s.acc_matvecs += r.matvecs;
+        s.acc_ms += r.mv_ms;
+        if (r.rnorm > kEdgeTol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
+        if (flops_per_mv) *flops_per_mv = plan->flops;
+        return r;
+    }
     env_make_operand(Lj, c->prec, ch.st);
     env_make_operand(Rj, c->prec, ch.st);
     auto plan = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), Lj.lay, Rj.lay, c->prec, ch.st);
     std::unique_ptr<HeffPlan> acc;
-    if (c->prec != DMRG_FP64 && p->refine_iters > 0)
+    if (c->prec != DMRG_FP64 && p->refine_iters > 0) {
+        env_make_operand(Lj, PREC_F32, ch.st);
+        env_make_operand(Rj, PREC_F32, ch.st);
         acc = make_heff_plan(ch.bond[j], ch.bond[j + 2], c->qn, c->pair(j), Lj.lay, Rj.lay, PREC_F32, ch.st);
+    }
     DavResult r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter,
                            ch.err.as<unsigned>(), ch.st, acc.get(), p->refine_iters);
+    Lj.drop_operands();
+    Rj.drop_operands();
     s.matvecs += r.matvecs;
     s.mv_ms += r.mv_ms;
     s.acc_matvecs += r.acc_matvecs;
@@ -203,7 +258,7 @@ DavResult solve_bond(dmrg_ctx* c, Chain& ch, int j, EnvSlab& Lj, EnvSlab& Rj, DB
 
 // Split psi at bond j, store A/B/Lambda in the chain, update the environment behind the move.
 void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_max, bool accurate, StepStats& s,
-                    SplitResult* out = nullptr) {
+                    SplitResult* out = nullptr, bool edge = false) {
     cudaStream_t st = ch.st;
     const Sec bl = ch.bond[j], br = ch.bond[j + 2];
     long long na, nb, nl;
@@ -212,7 +267,7 @@ void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_
     A.ensure(std::max<long long>(1, na) * 8, st);
     B.ensure(std::max<long long>(1, nb) * 8, st);
     // mixed-precision modes: FP32 Jacobi on ordinary bonds; FP64 at shared (accurate) bonds
-    const bool fp32 = c->prec != DMRG_FP64 && !accurate && !c->svd_fp64;
+    const bool fp32 = c->prec != DMRG_FP64 && !accurate && !c->svd_fp64 && !(edge && fp64_edge_split(c));
     SplitResult r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
                               right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st, fp32);
     if (fp32) {
@@ -238,15 +293,20 @@ void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_
     s.trunc = std::max(s.trunc, r.trunc);
     s.m = std::max(s.m, (int)r.mid.total());
     if (right) {
-        env_alloc(*ch.Lenv[j + 1], r.mid, c->W[j].fr, c->prec, st);
-        env_update_left(bl, r.mid, c->qn, c->W[j], *ch.Lenv[j], A.as<double>(), *ch.Lenv[j + 1], c->prec,
+        env_alloc(*ch.Lenv[j + 1], r.mid, c->W[j].fr, eprec(c), st);
+        env_update_left(bl, r.mid, c->qn, c->W[j], *ch.Lenv[j], A.as<double>(), *ch.Lenv[j + 1], eprec(c),
                         ch.err.as<unsigned>(), st);
         ch.oc = j + 1;
+        // R[j+1] belongs to the bond left of the new centre's two-site window and is rebuilt
+        // before it is read again (R[j+2] stays: a step back at bond j reads it)
+        if (j + 1 <= ch.q) ch.Renv[j + 1]->release();
     } else {
-        env_alloc(*ch.Renv[j + 1], r.mid, c->W[j + 1].fl, c->prec, st);
-        env_update_right(r.mid, br, c->qn, c->W[j + 1], *ch.Renv[j + 2], B.as<double>(), *ch.Renv[j + 1], c->prec,
+        env_alloc(*ch.Renv[j + 1], r.mid, c->W[j + 1].fl, eprec(c), st);
+        env_update_right(r.mid, br, c->qn, c->W[j + 1], *ch.Renv[j + 2], B.as<double>(), *ch.Renv[j + 1], eprec(c),
                          ch.err.as<unsigned>(), st);
         ch.oc = j;
+        // L[j+1] likewise (L[j] stays); the chain's outer environments (L[p], R[q+1]) are kept
+        if (j + 1 > ch.p) ch.Lenv[j + 1]->release();
     }
     ch.site[j] = std::move(A);
     ch.site[j + 1] = std::move(B);
@@ -262,15 +322,16 @@ void form_psi(dmrg_ctx* c, Chain& ch, int j, DBuf& psi) {
 
 // One two-site DMRG step at bond j (Sec. II): form Psi, Davidson, SVD + truncation, gauge move,
 // projected-operator update.
-void bond_step(dmrg_ctx* c, Chain& ch, int j, bool right, const dmrg_sweep_params* p, bool accurate = false) {
+void bond_step(dmrg_ctx* c, Chain& ch, int j, bool right, const dmrg_sweep_params* p, bool accurate = false,
+               bool edge = false) {
     PD_REQUIRE(ch.oc == (right ? j : j + 1), DMRG_ERR_STATE, "orthogonality centre not at the bond");
     DBuf psi;
     form_psi(c, ch, j, psi);
     StepStats& s = ch.acc;
-    DavResult r = solve_bond(c, ch, j, *ch.Lenv[j], *ch.Renv[j + 2], psi, p, s, nullptr);
+    DavResult r = solve_bond(c, ch, j, *ch.Lenv[j], *ch.Renv[j + 2], psi, p, s, nullptr, edge);
     s.energy = r.theta;
     s.steps++;
-    split_and_move(c, ch, j, right, psi, p->m_max, accurate, s);
+    split_and_move(c, ch, j, right, psi, p->m_max, accurate, s, nullptr, edge);
 }
 
 // Move the centre across bond j by an untruncated SVD (no Davidson).
@@ -293,6 +354,7 @@ void copy_env(EnvSlab& dst, const EnvSlab& src, cudaStream_t st) {
     dst.buf.ensure(bytes, st);
     PD_CK(cudaMemcpyAsync(dst.buf.p, src.buf.p, bytes, cudaMemcpyDeviceToDevice, st));
     dst.op_valid = false;
+    dst.op32_valid = false;
     dst.valid = src.valid;
 }
 
@@ -329,12 +391,14 @@ double rayleigh_fp64(dmrg_ctx* c, Chain& ch, int j, const double* psi) {
 // Regions
 // ------------------------------------------------------------------------------------------
 void region_half_sweep(dmrg_ctx* c, Chain& r, bool right, const dmrg_sweep_params* p) {
+    // edge bonds: (q-1, q) when bond q+1 is a boundary, (p, p+1) when bond p is one
+    auto edge = [&](int j) { return (j == r.q - 1 && r.q + 1 < c->L) || (j == r.p && r.p > 0); };
     if (right) {
         PD_REQUIRE(r.oc == r.p, DMRG_ERR_STATE, "region centre not at its left end");
-        for (int j = r.p; j < r.q; ++j) bond_step(c, r, j, true, p);
+        for (int j = r.p; j < r.q; ++j) bond_step(c, r, j, true, p, false, edge(j));
     } else {
         PD_REQUIRE(r.oc == r.q, DMRG_ERR_STATE, "region centre not at its right end");
-        for (int j = r.q - 1; j >= r.p; --j) bond_step(c, r, j, false, p);
+        for (int j = r.q - 1; j >= r.p; --j) bond_step(c, r, j, false, p, false, edge(j));
     }
 }
 
@@ -409,21 +473,38 @@ void do_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fid_out, d
     copy_site(guess, psi, P.size, st);
     EnvSlab& Lj = *left.Lenv[b - 1];
     EnvSlab& Rj = *right.Renv[b + 1];
-    env_make_operand(Lj, c->prec, st);
-    env_make_operand(Rj, c->prec, st);
-    auto plan = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, c->prec, st);
-    std::unique_ptr<HeffPlan> accp;
-    if (c->prec != DMRG_FP64 && p->refine_iters > 0)
-        accp = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, PREC_F32, st);
-    DavResult r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter,
-                           left.err.as<unsigned>(), st, accp.get(), p->refine_iters);
     StepStats& s = left.acc;
-    s.matvecs += r.matvecs;
-    s.mv_ms += r.mv_ms;
-    s.acc_matvecs += r.acc_matvecs;
-    s.acc_ms += r.acc_ms;
-    s.mv_flops += plan->flops * r.matvecs;
-    if (r.rnorm > p->dav_tol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
+    DavResult r;
+    if (fp64_solve(c)) {
+        EnvSlab l64, r64;
+        const EnvSlab& L = env64_view(Lj, l64, st);
+        const EnvSlab& R = env64_view(Rj, r64, st);
+        auto plan = make_heff_plan(bl, br, c->qn, c->pair(b - 1), L.lay, R.lay, DMRG_FP64, st);
+        r = davidson(*plan, L, R, psi.as<double>(), c->kmax, kEdgeTol, edge_iters(p), left.err.as<unsigned>(), st);
+        s.acc_matvecs += r.matvecs;
+        s.acc_ms += r.mv_ms;
+        if (r.rnorm > kEdgeTol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
+    } else {
+        env_make_operand(Lj, c->prec, st);
+        env_make_operand(Rj, c->prec, st);
+        auto plan = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, c->prec, st);
+        std::unique_ptr<HeffPlan> accp;
+        if (c->prec != DMRG_FP64 && p->refine_iters > 0) {
+            env_make_operand(Lj, PREC_F32, st);
+            env_make_operand(Rj, PREC_F32, st);
+            accp = make_heff_plan(bl, br, c->qn, c->pair(b - 1), Lj.lay, Rj.lay, PREC_F32, st);
+        }
+        r = davidson(*plan, Lj, Rj, psi.as<double>(), c->kmax, p->dav_tol, p->dav_max_iter, left.err.as<unsigned>(),
+                     st, accp.get(), p->refine_iters);
+        Lj.drop_operands();
+        Rj.drop_operands();
+        s.matvecs += r.matvecs;
+        s.mv_ms += r.mv_ms;
+        s.acc_matvecs += r.acc_matvecs;
+        s.acc_ms += r.acc_ms;
+        s.mv_flops += plan->flops * r.matvecs;
+        if (r.rnorm > p->dav_tol * std::max(1.0, std::fabs(r.theta))) s.nonconv++;
+    }
     double ov = dot_host(guess.as<double>(), psi.as<double>(), P.size, st);
     double fid = 1.0 - std::fabs(ov);
     s.energy = r.theta;
@@ -443,10 +524,10 @@ void do_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fid_out, d
     upload(lamd, sr.lam, st);
     // new projected operators for both sides (Sec. II: each side's operators in its own basis)
     std::unique_ptr<EnvSlab> Lnew(new EnvSlab()), Rnew(new EnvSlab());
-    env_alloc(*Lnew, sr.mid, c->W[b - 1].fr, c->prec, st);
-    env_update_left(bl, sr.mid, c->qn, c->W[b - 1], Lj, A.as<double>(), *Lnew, c->prec, left.err.as<unsigned>(), st);
-    env_alloc(*Rnew, sr.mid, c->W[b].fl, c->prec, st);
-    env_update_right(sr.mid, br, c->qn, c->W[b], Rj, B.as<double>(), *Rnew, c->prec, left.err.as<unsigned>(), st);
+    env_alloc(*Lnew, sr.mid, c->W[b - 1].fr, eprec(c), st);
+    env_update_left(bl, sr.mid, c->qn, c->W[b - 1], Lj, A.as<double>(), *Lnew, eprec(c), left.err.as<unsigned>(), st);
+    env_alloc(*Rnew, sr.mid, c->W[b].fl, eprec(c), st);
+    env_update_right(sr.mid, br, c->qn, c->W[b], Rj, B.as<double>(), *Rnew, eprec(c), left.err.as<unsigned>(), st);
     // psi_3 = A Lambda for the left region, psi_4 = Lambda B for the right region
     const SiteLayout SA = site_layout(bl, sr.mid, c->qn), SB = site_layout(sr.mid, br, c->qn);
     DBuf psi3, psi4;
@@ -532,8 +613,8 @@ void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
         left_end[k].ensure(std::max<long long>(1, SB.size) * 8, st);
         scale_site(sr.mid, br, c->qn, B.as<double>(), lamd.as<double>(), false, left_end[k].as<double>(), st);
         left_env[k].reset(new EnvSlab());
-        env_alloc(*left_env[k], sr.mid, c->W[j].fr, c->prec, st);
-        env_update_left(bl, sr.mid, c->qn, c->W[j], *ch.Lenv[j], A.as<double>(), *left_env[k], c->prec,
+        env_alloc(*left_env[k], sr.mid, c->W[j].fr, eprec(c), st);
+        env_update_left(bl, sr.mid, c->qn, c->W[j], *ch.Lenv[j], A.as<double>(), *left_env[k], eprec(c),
                         ch.err.as<unsigned>(), st);
         // serial chain continues left with A Lambda
         DBuf AL;
@@ -541,8 +622,8 @@ void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
         scale_site(bl, sr.mid, c->qn, A.as<double>(), lamd.as<double>(), true, AL.as<double>(), st);
         ch.bond[b] = sr.mid;
         ch.lam[b] = sr.lam;
-        env_alloc(*ch.Renv[b], sr.mid, c->W[j + 1].fl, c->prec, st);
-        env_update_right(sr.mid, br, c->qn, c->W[j + 1], *ch.Renv[j + 2], B.as<double>(), *ch.Renv[b], c->prec,
+        env_alloc(*ch.Renv[b], sr.mid, c->W[j + 1].fl, eprec(c), st);
+        env_update_right(sr.mid, br, c->qn, c->W[j + 1], *ch.Renv[j + 2], B.as<double>(), *ch.Renv[b], eprec(c),
                          ch.err.as<unsigned>(), st);
         ch.site[j] = std::move(AL);
         ch.site[j + 1] = std::move(B);
@@ -695,6 +776,8 @@ dmrg_status dmrg_init_mpo(dmrg_ctx** out, const dmrg_mpo_desc* mpo, const dmrg_c
     C->svd_fp64 = cfg->svd_fp64 != 0;
     C->emu = cfg->fp64_emulation != 0;
     C->svd_plain = cfg->svd_plain_jacobi != 0;
+    C->env64 = cfg->env_fp64 != 0;
+    C->acc_edges = std::max(0, std::min(2, cfg->accurate_edges));
     PD_REQUIRE(!C->emu || tc_available(), DMRG_ERR_STATE, "FP64 emulation needs sm_103 tensor cores");
     PD_REQUIRE(C->kmax >= 2 && C->kmax <= 32, DMRG_ERR_ARG, "kmax must be in [2, 32]");
     C->base = (cudaStream_t)cfg->stream;
@@ -754,9 +837,9 @@ dmrg_status dmrg_set_mps(dmrg_ctx* c, const dmrg_mps_desc* m) {
     make_boundary_envs(c, ch);
     build_right_envs(c, ch, center + 1);
     for (int j = 0; j < center; ++j) {
-        env_alloc(*ch.Lenv[j + 1], ch.bond[j + 1], c->W[j].fr, c->prec, ch.st);
+        env_alloc(*ch.Lenv[j + 1], ch.bond[j + 1], c->W[j].fr, eprec(c), ch.st);
         env_update_left(ch.bond[j], ch.bond[j + 1], c->qn, c->W[j], *ch.Lenv[j], ch.site[j].as<double>(),
-                        *ch.Lenv[j + 1], c->prec, ch.err.as<unsigned>(), ch.st);
+                        *ch.Lenv[j + 1], eprec(c), ch.err.as<unsigned>(), ch.st);
     }
     check_err_word(ch.err.as<unsigned>(), ch.st);
     c->dir = center < c->L - 1 ? 1 : -1;

@@ -495,6 +495,7 @@ bool run_gemm64_emu(GemmBatch& g, const double* A, const double* B, double* C, c
         g.emu.reset(build_plan(g, st).release(), free_emu_plan);
     EmuPlan& P = *g.emu;
     if (!P.usable) return false;
+    const int cls = g_prof_class == PROF_ENV ? PROF_ENV : PROF_F64;
     void* tok = prof_on() ? prof_start(st) : nullptr;
     PD_CK(cudaMemsetAsync(P.rowmax.p, 0, (size_t)std::max<long long>(1, P.a_rows + P.b_rows) * 8, st));
     PD_CK(cudaMemsetAsync(P.cmax.p, 0, (size_t)(P.na_cls + P.nb_cls) * 8, st));
@@ -538,7 +539,7 @@ bool run_gemm64_emu(GemmBatch& g, const double* A, const double* B, double* C, c
                                                            P.cls_a.as<int>(), P.cls_b.as<int>(), P.na_cls,
                                                            P.cmax.as<unsigned long long>(), C);
     PD_LAUNCHED();
-    if (tok) prof_stop(tok, st, PROF_F64, g.flops);
+    if (tok) prof_stop(tok, st, cls, g.flops);
     check_err_word(P.err.as<unsigned>(), st);
     return true;
 }

@@ -132,7 +132,7 @@ void run_gemm64(GemmBatch& g, const double* A, const double* B, double* C, cudaS
     g.upload_tiles(64, 64, st);
     void* tok = prof_on() ? prof_start(st) : nullptr;
     launch_gemm_simt<double>(g.dprobs.as<GProb>(), g.dsegs.as<GSeg>(), g.dtiles.as<GTile>(), g.ntiles, A, B, C, st);
-    if (tok) prof_stop(tok, st, PROF_F64, g.flops);
+    if (tok) prof_stop(tok, st, g_prof_class == PROF_ENV ? PROF_ENV : PROF_F64, g.flops);
 }
 
 void run_gemm32(GemmBatch& g, const float* A, const float* B, float* C, cudaStream_t st) {
@@ -395,6 +395,69 @@ void orthonormalize_factor(const Sec& bl, const Sec& br, const std::vector<int>&
     PD_CK(cudaStreamSynchronize(st));
 }
 
+void convert_flat(const void* src, Num in, void* dst, Num out, long long n, cudaStream_t st) {
+    if (n <= 0) return;
+    CopyList cl;
+    const long long chunk = 1 << 20;
+    for (long long s0 = 0; s0 < n; s0 += chunk) {
+        CopyJob j{};
+        j.src = s0; j.dst = s0; j.rows = 1; j.cols = (int)std::min(chunk, n - s0);
+        j.srs = 0; j.scs = 1; j.drs = 0; j.dcs = 1; j.zero_to = 0; j.scale = 1.0;
+        cl.add(j);
+    }
+    cl.up(st);
+    PD_REQUIRE(in == Num::F64 || in == Num::F32, DMRG_ERR_ARG, "convert_flat: source must be FP64 or FP32");
+    if (in == Num::F64) run_copy<double>(cl, static_cast<const double*>(src), dst, out, st);
+    else run_copy<float>(cl, static_cast<const float*>(src), dst, out, st);
+}
+
+void orthonormalize_square(const std::vector<SvdSec>& ss, double* V, cudaStream_t st) {
+    std::vector<NsJob> jobs;
+    std::vector<DevJob> djobs;
+    GemmBatch gG, gX;
+    long long tot = 0;
+    int mx = 1;
+    for (const auto& x : ss) {
+        if (x.n <= 0) continue;
+        const int n = x.n;
+        jobs.push_back({x.v_off, n, 0});
+        djobs.push_back({x.v_off, n, 0});
+        mx = std::max(mx, n * n);
+        // G = V^T V:  G(i, j) = sum_k V(k, i) V(k, j), V column-major (V(r, c) = V[off + r + c n])
+        gG.add(n, n, x.v_off, n, 1, n, 1, n, 1, {GSeg{x.v_off, x.v_off, n, 0}});
+        // V' = V T:   V'(r, c) = sum_u V(r, u) T(u, c), T symmetric
+        gX.add(n, n, x.v_off, 1, n, n, 1, 1, n, {GSeg{x.v_off, x.v_off, n, 0}});
+        tot = std::max(tot, x.v_off + (long long)n * n);
+    }
+    if (jobs.empty()) return;
+    DBuf G, T, out, dev, dj, djd;
+    G.ensure(tot * 8, st);
+    T.ensure(tot * 8, st);
+    out.ensure(tot * 8, st);
+    dev.ensure(jobs.size() * 8, st);
+    upload(dj, jobs, st);
+    upload(djd, djobs, st);
+    std::vector<double> hdev(jobs.size());
+    for (int iter = 0; iter < 8; ++iter) {
+        run_gemm64(gG, V, V, G.as<double>(), st);
+        k_gram_dev<<<(unsigned)jobs.size(), 256, 0, st>>>(djd.as<DevJob>(), G.as<double>(), dev.as<double>());
+        PD_LAUNCHED();
+        PD_CK(cudaMemcpyAsync(hdev.data(), dev.p, jobs.size() * 8, cudaMemcpyDeviceToHost, st));
+        PD_CK(cudaStreamSynchronize(st));
+        double worst = 0.0;
+        for (double v : hdev) worst = std::max(worst, v);
+        PD_REQUIRE(std::isfinite(worst) && worst < 0.5, DMRG_ERR_NUMERIC,
+                   "FP32 Jacobi rotations too far from orthogonal for the FP64 polish");
+        if (worst < 1e-14) break;
+        k_ns_prep<<<dim3(gridn(mx, 256), (unsigned)jobs.size()), 256, 0, st>>>(dj.as<NsJob>(), G.as<double>(),
+                                                                               T.as<double>());
+        PD_LAUNCHED();
+        run_gemm64(gX, V, T.as<double>(), out.as<double>(), st);
+        for (const auto& j : jobs)
+            PD_CK(cudaMemcpyAsync(V + j.off, out.as<double>() + j.off, (size_t)j.k * j.k * 8, cudaMemcpyDeviceToDevice, st));
+    }
+}
+
 void scale_vec(double* x, long long n, double s, cudaStream_t st) {
     if (n <= 0) return;
     k_scale_plain<<<gridn(n), 256, 0, st>>>(x, n, s);
@@ -427,8 +490,11 @@ std::unique_ptr<HeffPlan> make_heff_plan(const Sec& bl, const Sec& br, const std
     P->R = &R;
     P->ld_psi = pad_ld(bl.maxm(), prec);
     P->ld_y = pad_ld(br.maxm(), prec);
-    PD_REQUIRE(L.ld == pad_ld(bl.maxm(), prec) && R.ld == pad_ld(br.maxm(), prec), DMRG_ERR_STATE,
-               "environment slab stride does not match the bond");
+    // FP64 plans read any stride (also the tensor-core layout of FP64-accurate mixed-mode
+    // environments); the tensor-core plans need the 64-padded operand layout
+    PD_REQUIRE(prec == DMRG_FP64 ? (L.ld >= bl.maxm() && R.ld >= br.maxm())
+                                 : (L.ld == pad_ld(bl.maxm(), prec) && R.ld == pad_ld(br.maxm(), prec)),
+               DMRG_ERR_STATE, "environment slab stride does not match the bond");
     const auto& pb = P->psi.blk;
     const int nb = (int)pb.size();
 
@@ -591,6 +657,10 @@ static const void* env_operand(const EnvSlab& e, int prec) {
         PD_REQUIRE(e.op_valid, DMRG_ERR_STATE, "bf16 operand copy of an environment is stale");
         return e.op.p;
     }
+    if ((prec == DMRG_TF32 || prec == PREC_F32) && e.num == Num::F64) {
+        PD_REQUIRE(e.op32_valid, DMRG_ERR_STATE, "FP32 operand copy of an environment is stale");
+        return e.op32.p;
+    }
     return e.buf.p;
 }
 
@@ -611,10 +681,12 @@ void heff_apply(HeffPlan& P, const EnvSlab& L, const EnvSlab& R, const double* x
         DBuf y32;
         y32.ensure(std::max<long long>(1, P.psi.size) * 4, st);
         PD_CK(cudaMemsetAsync(y32.p, 0, std::max<long long>(1, P.psi.size) * 4, st));
-        run_gemm32(P.lstage, P.psiT.as<float>(), L.buf.as<float>(), P.X.as<float>(), st);
-        run_gemm32(P.ldirect, P.psiT.as<float>(), L.buf.as<float>(), P.Y.as<float>(), st);
+        const float* Lf = static_cast<const float*>(env_operand(L, PREC_F32));
+        const float* Rf = static_cast<const float*>(env_operand(R, PREC_F32));
+        run_gemm32(P.lstage, P.psiT.as<float>(), Lf, P.X.as<float>(), st);
+        run_gemm32(P.ldirect, P.psiT.as<float>(), Lf, P.Y.as<float>(), st);
         run_mix<float>(P.mix, P.X.as<float>(), P.Y.p, Num::F32, st);
-        run_gemm32(P.rstage, R.buf.as<float>(), P.Y.as<float>(), y32.as<float>(), st);
+        run_gemm32(P.rstage, Rf, P.Y.as<float>(), y32.as<float>(), st);
         if (!P.unpack.d.p) {
             CopyJob j{};
             j.src = 0; j.dst = 0; j.rows = 1; j.cols = (int)P.psi.size; j.srs = 0; j.scs = 1; j.drs = 0; j.dcs = 1;
@@ -654,11 +726,13 @@ void env_alloc(EnvSlab& e, const Sec& b, const std::vector<int>& flux, int prec,
     e.buf.ensure(bytes, st);
     PD_CK(cudaMemsetAsync(e.buf.p, 0, bytes, st));
     e.op_valid = false;
+    e.op32_valid = false;
     e.valid = true;
 }
 
 void env_make_operand(EnvSlab& e, int prec, cudaStream_t st) {
-    if (prec != DMRG_BF16 || e.op_valid) return;
+    const bool bf = prec == DMRG_BF16, f32 = (prec == DMRG_TF32 || prec == PREC_F32) && e.num == Num::F64;
+    if ((!bf && !f32) || (bf && e.op_valid) || (f32 && e.op32_valid)) return;
     CopyList c;
     long long n = std::max<long long>(1, e.lay.rows) * e.lay.ld;
     // one flat row-major copy of the whole slab (padding included, zeros stay zeros)
@@ -670,9 +744,11 @@ void env_make_operand(EnvSlab& e, int prec, cudaStream_t st) {
         c.add(j);
     }
     c.up(st);
-    e.op.ensure(n * 2, st);
-    run_copy<float>(c, e.buf.as<float>(), e.op.p, Num::BF16, st);
-    e.op_valid = true;
+    DBuf& dst = bf ? e.op : e.op32;
+    dst.ensure(n * (bf ? 2 : 4), st);
+    if (e.num == Num::F64) run_copy<double>(c, e.buf.as<double>(), dst.p, bf ? Num::BF16 : Num::F32, st);
+    else run_copy<float>(c, e.buf.as<float>(), dst.p, Num::BF16, st);
+    (bf ? e.op_valid : e.op32_valid) = true;
 }
 
 void env_from_packed(EnvSlab& e, const double* packed, cudaStream_t st) {
@@ -686,6 +762,7 @@ void env_from_packed(EnvSlab& e, const double* packed, cudaStream_t st) {
     c.up(st);
     run_copy<double>(c, packed, e.buf.p, e.num, st);
     e.op_valid = false;
+    e.op32_valid = false;
     e.valid = true;
 }
 
@@ -716,24 +793,35 @@ void env_boundary(EnvSlab& e, const Sec& b, const std::vector<int>& flux, int pr
     }
     PD_CK(cudaStreamSynchronize(st));
     e.op_valid = false;
+    e.op32_valid = false;
 }
 
 // ------------------------------------------------------------------------------------------
 // Environment updates (Sec. II operator transformation)
 // ------------------------------------------------------------------------------------------
 // Environment updates compound their rounding errors site after site, so they run at FP32
-// accuracy or better in every mode (FP64 SIMT in FP64 mode, FP32 SIMT in the mixed modes).
+// accuracy or better in every mode: FP64 GEMMs in FP64 mode and, with FP64-accurate environments,
+// in the mixed modes (PREC_ENV64, on the tensor-core operand layout); FP32 SIMT GEMMs otherwise.
 static void run_env_gemm(GemmBatch& g, int prec, const void* A, long long arows, int lda, const void* B,
                          long long brows, int ldb, void* C, unsigned* err, cudaStream_t st) {
     (void)arows; (void)lda; (void)brows; (void)ldb; (void)err;
     if (g.empty()) return;
-    if (prec == DMRG_FP64) run_gemm64(g, (const double*)A, (const double*)B, (double*)C, st);
+    if (env_num(prec) == Num::F64) run_gemm64(g, (const double*)A, (const double*)B, (double*)C, st);
     else run_gemm32(g, (const float*)A, (const float*)B, (float*)C, st);
 }
 
+namespace {
+// Environment-update GEMMs are tallied as such; the calling thread's class is restored on return.
+struct EnvProfClass {
+    int saved = g_prof_class;
+    EnvProfClass() { g_prof_class = PROF_ENV; }
+    ~EnvProfClass() { g_prof_class = saved; }
+};
+}  // namespace
+
 void env_update_left(const Sec& ba, const Sec& bb, const std::vector<int>& qn, const SiteMPO& W,
                      const EnvSlab& Lin, const double* A, EnvSlab& Lout, int prec, unsigned* err, cudaStream_t st) {
-    g_prof_class = PROF_ENV;
+    EnvProfClass prof_class;
     const int d = (int)qn.size();
     const SiteLayout S = site_layout(ba, bb, qn);
     const EnvLayout& Li = Lin.lay;
@@ -837,12 +925,13 @@ void env_update_left(const Sec& ba, const Sec& bb, const std::vector<int>& qn, c
     else run_mix<float>(mx, t1b.as<float>(), t2b.p, tn, st);
     run_env_gemm(g3, prec, t2b.p, trow, ldT, sl.p, srows, ldS, Lout.buf.p, err, st);
     Lout.op_valid = false;
+    Lout.op32_valid = false;
     PD_CK(cudaStreamSynchronize(st));   // scratch and job lists are released on return
 }
 
 void env_update_right(const Sec& ba, const Sec& bc, const std::vector<int>& qn, const SiteMPO& W,
                       const EnvSlab& Rin, const double* Bt, EnvSlab& Rout, int prec, unsigned* err, cudaStream_t st) {
-    g_prof_class = PROF_ENV;
+    EnvProfClass prof_class;
     const int d = (int)qn.size();
     const SiteLayout S = site_layout(ba, bc, qn);
     const EnvLayout& Ri = Rin.lay;
@@ -946,6 +1035,7 @@ void env_update_right(const Sec& ba, const Sec& bc, const std::vector<int>& qn, 
     else run_mix<float>(mx, t1b.as<float>(), t2b.p, tn, st);
     run_env_gemm(g3, prec, t2b.p, trow, ldT, sl.p, srows, ldS, Rout.buf.p, err, st);
     Rout.op_valid = false;
+    Rout.op32_valid = false;
     PD_CK(cudaStreamSynchronize(st));
 }
 
@@ -1327,9 +1417,8 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     QrPlan qp;
     DBuf dxsecs, dVJ;
     std::vector<SvdSec> xs;
-    if (g_svd_qr && woff > 0) {
-        if (fp32) qp.build<float>(ss, st);
-        else qp.build<double>(ss, st);
+    if (g_svd_qr && woff > 0 && fp32) {
+        qp.build<float>(ss, st);
         if (qp.ok) {
             xs = ss;
             for (auto& x : xs) {
@@ -1343,21 +1432,11 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     const bool use_qr = qp.ok && !xs.empty();
     const SvdSec* jsecs = use_qr ? dxsecs.as<SvdSec>() : dsecs.as<SvdSec>();
     const int jmaxp = use_qr ? maxn : maxp;
-    if (fp32) {
-        run_copy<double>(gather, psi, dW.p, Num::F32, st);
-        float* JW = dW.as<float>();
-        float* JV = dV.as<float>();
-        if (use_qr) {
-            qp.factor<float>(dW.as<float>(), st);
-            qp.form_rt<float>(dW.as<float>(), dV.as<float>(), st);
-            JW = dV.as<float>();
-            JV = dVJ.as<float>();
-        }
-        launch_svd_init_v<float>(jsecs, nsec, maxn, JV, st);
-        // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it; the
-        // kept factor that joins a block is re-orthonormalised in FP64 afterwards
-        const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)jmaxp));
-        // block Jacobi: one task per block pair, n / 16 - 1 rounds per sweep
+    // FP32 block Jacobi (one task per block pair, n / 16 - 1 rounds per sweep) of the matrices
+    // secs_d (p x n at w_off of JW, rotations accumulated at v_off of JV); rot: sweep histogram.
+    auto block_jacobi32 = [&](const SvdSec* secs_d, float* JW, float* JV, int max_rows, int* rot) {
+        // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it
+        const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)max_rows));
         std::vector<BjSec> bs(nsec);
         std::vector<int> task_sec;
         int nrounds = 0;
@@ -1377,9 +1456,23 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         dgmax.ensure(std::max(1, nsec) * 4, st);
         PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
         PD_CK(cudaMemsetAsync(dflops.p, 0, 8, st));
-        launch_bjacobi(jsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, jmaxp, maxn, 40, 2, JW,
-                       JV, tol, 8.0f * FLT_EPSILON, dgmax.as<float>(), drot.as<int>(), drot.as<int>() + max_sweeps, bar,
-                       jerr, dflops.as<unsigned long long>(), st);
+        launch_bjacobi(secs_d, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, maxn, 40, 2, JW,
+                       JV, tol, 8.0f * FLT_EPSILON, dgmax.as<float>(), rot, rot + max_sweeps, bar, jerr,
+                       dflops.as<unsigned long long>(), st);
+    };
+    if (fp32) {
+        run_copy<double>(gather, psi, dW.p, Num::F32, st);
+        float* JW = dW.as<float>();
+        float* JV = dV.as<float>();
+        if (use_qr) {
+            qp.factor<float>(dW.as<float>(), st);
+            qp.form_rt<float>(dW.as<float>(), dV.as<float>(), st);
+            JW = dV.as<float>();
+            JV = dVJ.as<float>();
+        }
+        launch_svd_init_v<float>(jsecs, nsec, maxn, JV, st);
+        // the kept factor that joins a block is re-orthonormalised in FP64 afterwards
+        block_jacobi32(jsecs, JW, JV, jmaxp, drot.as<int>());
         if (use_qr) {
             DBuf dWo;
             dWo.ensure(std::max<long long>(1, woff) * es, st);
@@ -1394,24 +1487,34 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
             dM.ensure(woff * 8, st);
             PD_CK(cudaMemcpyAsync(dM.p, dW.p, woff * 8, cudaMemcpyDeviceToDevice, st));
         }
-        double* JW = dW.as<double>();
-        double* JV = dV.as<double>();
-        if (use_qr) {
-            qp.factor<double>(dW.as<double>(), st);
-            qp.form_rt<double>(dW.as<double>(), dV.as<double>(), st);
-            JW = dV.as<double>();
-            JV = dVJ.as<double>();
+        const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+        if (g_svd_qr && woff > 0) {
+            // FP32 block Jacobi on an FP32 copy, its rotations orthonormalised in FP64 (Newton-Schulz),
+            // W <- W Q in FP64, then the FP64 one-sided Jacobi from V = Q: the columns start
+            // orthogonal to FP32 accuracy, so the FP64 sweeps converge in the quadratic regime
+            DBuf w32, v32, rot32, dW1;
+            w32.ensure(woff * 4, st);
+            v32.ensure(std::max<long long>(1, voff) * 4, st);
+            rot32.ensure((max_sweeps + 1) * 4, st);
+            PD_CK(cudaMemsetAsync(rot32.p, 0, (max_sweeps + 1) * 4, st));
+            convert_flat(dW.p, Num::F64, w32.p, Num::F32, woff, st);
+            launch_svd_init_v<float>(dsecs.as<SvdSec>(), nsec, maxn, v32.as<float>(), st);
+            block_jacobi32(dsecs.as<SvdSec>(), w32.as<float>(), v32.as<float>(), maxp, rot32.as<int>());
+            convert_flat(v32.p, Num::F32, dV.p, Num::F64, voff, st);
+            orthonormalize_square(ss, dV.as<double>(), st);
+            GemmBatch gwq;
+            for (const auto& x : ss)
+                if (x.n > 0)   // W1(r, c) = sum_u W(r, u) Q(u, c)
+                    gwq.add(x.p, x.n, x.w_off, 1, x.p, x.n, 1, 1, x.p, {GSeg{x.w_off, x.v_off, x.n, 0}});
+            dW1.ensure(woff * 8, st);
+            run_gemm64(gwq, dW.as<double>(), dV.as<double>(), dW1.as<double>(), st);
+            dW = std::move(dW1);
+        } else {
+            launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
         }
-        launch_svd_init_v<double>(jsecs, nsec, maxn, JV, st);
-        const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)jmaxp);
-        launch_jacobi<double>(jsecs, nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps, JW, JV, tol, 0.0, nullptr,
-                              drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr, st);
-        if (use_qr) {
-            DBuf dWo;
-            dWo.ensure(std::max<long long>(1, woff) * es, st);
-            qp.finish<double>(dW.as<double>(), dV.as<double>(), dVJ.as<double>(), dWo.as<double>(), st);
-            dW = std::move(dWo);
-        }
+        launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps, dW.as<double>(),
+                              dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr,
+                              st);
         launch_svd_finish<double>(dsecs.as<SvdSec>(), nsec, dW.as<double>(), dsig.as<double>(), dord.as<int>(), st);
         if (accurate && woff > 0)
             accurate_refine(ss, dsecs.as<SvdSec>(), dW.as<double>(), dV.as<double>(), dsig.as<double>(),

@@ -128,6 +128,9 @@ inline size_t num_size(Num t) { return t == Num::F64 ? 8 : (t == Num::F32 ? 4 : 
 // Internal matvec arithmetic for the accurate Davidson refinement of the mixed modes: FP32
 // operands and accumulation on the CUDA cores (same slab layout as TF32).
 constexpr int PREC_F32 = 3;
+// Environment arithmetic of the mixed modes with FP64-accurate environments: the tensor-core
+// operand layout (rows and leading dimension padded to 64), FP64 storage, FP64 GEMMs.
+constexpr int PREC_ENV64 = 4;
 inline int pad_ld(int x, int prec) {
     int a = (prec == DMRG_FP64) ? 2 : 64;
     x = std::max(x, 1);
@@ -138,7 +141,7 @@ inline int kpad(int K, int prec) { return prec == DMRG_FP64 ? K : (K + 63) / 64 
 inline Num mv_num(int prec) {
     return prec == DMRG_FP64 ? Num::F64 : ((prec == DMRG_TF32 || prec == PREC_F32) ? Num::F32 : Num::BF16);
 }
-inline Num env_num(int prec) { return prec == DMRG_FP64 ? Num::F64 : Num::F32; }
+inline Num env_num(int prec) { return (prec == DMRG_FP64 || prec == PREC_ENV64) ? Num::F64 : Num::F32; }
 
 // ------------------------------------------------------------------------------------------
 // Grouped GEMM batch (host list -> device arrays -> FP64 SIMT or tcgen05 launch)
@@ -243,10 +246,26 @@ struct EnvSlab {
     DBuf buf;                 // storage
     DBuf op;                  // bf16 operand copy (BF16 mode)
     bool op_valid = false;
+    DBuf op32;                // FP32 operand copy of FP64 storage (TF32 mode, FP32 refinement)
+    bool op32_valid = false;
     bool valid = false;
     void rebind(cudaStream_t s) {
         buf.rebind(s);
         op.rebind(s);
+        op32.rebind(s);
+    }
+    // The operand copies are rebuilt on demand (one flat copy each); dropping them between steps
+    // keeps one storage copy per environment resident.
+    void drop_operands() {
+        op.release();
+        op32.release();
+        op_valid = op32_valid = false;
+    }
+    // An environment the sweep has moved past (it is rebuilt before it is read again).
+    void release() {
+        drop_operands();
+        buf.release();
+        valid = false;
     }
 };
 
@@ -336,6 +355,11 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
 // br), X <- (3I - X X^T)/2 X for a right factor (kept index on bl).
 void orthonormalize_factor(const Sec& bl, const Sec& br, const std::vector<int>& qn, double* X, bool left,
                            cudaStream_t st);
+// Flat element-type conversion of n elements (FP64 or FP32 source), stream-ordered.
+void convert_flat(const void* src, Num in, void* dst, Num out, long long n, cudaStream_t st);
+// Newton-Schulz orthonormalisation in FP64 of the square n x n matrices at v_off (column-major) of
+// V, one per sector of ss, until |V^T V - I|_max < 1e-14.
+void orthonormalize_square(const std::vector<SvdSec>& ss, double* V, cudaStream_t st);
 // Worst-case (untruncated) element counts of the split's A and B outputs.
 void svd_split_bounds(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
                       long long* a_elems, long long* b_elems, long long* lam_elems);

@@ -274,3 +274,29 @@ def test_region_state_export():
     assert abs(eng2.energy() - e_dense) <= 1e-11 * abs(e_dense)
     eng.close()
     eng2.close()
+
+
+def test_mixed_regions_fp64_edges_merge_predicts():
+    """bf16 regions with FP64-accurate environments and FP64 solves next to the boundaries (the
+    edge tensors psi_3, psi_4 of Eq. (merge) and the merges): the merge prediction
+    Psi' = psi'_3 V psi'_4 stays a good initial guess (fidelity 1 - |<Psi'|Psi>| below 1e-2 once
+    converged; the bf16-only solves leave it near 1), and the parallel-sweep energy -- a Rayleigh
+    quotient on FP64-accurate environments -- agrees with the FP64 oracle to 1e-5."""
+    L = 32
+    mpo = wl.heisenberg_chain(L)
+    qn = list(mpo.site.qn)
+    mps = wl.random_mps(L, qn, 0, 16, seed=0)
+    ref = O.SerialDMRG(mpo, mps)
+    for m in (32, 64, 64, 64):
+        r = ref.sweep(m)
+    W, flux, D = wl.pack_mpo(mpo)
+    eng = pd.Engine(W, flux, D, qn, 0, "bf16", 8, fp64_emulation=True, env_fp64=True, accurate_edges=True)
+    load_mps(eng, mps, qn)
+    dav = dict(dav_tol=1e-9, dav_max_iter=12, refine_iters=6, serial_regions=1)
+    eng.setup_regions(4, 1, 32, **dav)
+    for m in (32, 64, 64, 64, 64, 64):
+        g = eng.sweep(m, **dav)
+    assert g["max_fidelity"] <= 1e-2, g["max_fidelity"]
+    assert abs(g["energy"] - r["energy"]) <= 1e-5 * abs(r["energy"]), (g["energy"], r["energy"])
+    assert g["n_refine_matvec"] > 0
+    eng.close()
