@@ -34,6 +34,9 @@ NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (per GPU)
 FP64_PEAK_TFLOPS = 1.25                 # nominal FP64 rate of a GB300
 
 
+T_START = time.perf_counter()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -68,6 +71,9 @@ def parse():
     ap.add_argument("--acc-refine", type=int, default=12,
                     help="accuracy leg: FP32-accurate refinement iterations of the mixed sweep (after --dav-iters "
                          "tensor-core iterations)")
+    ap.add_argument("--time-budget-s", type=float, default=1700.0,
+                    help="wall-clock budget of the whole run: the accuracy leg's same-state sweeps are skipped "
+                         "(and the reason recorded) when they would end beyond it")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="sweeps mode: skip the FP64 evaluation and the FP64-vs-mixed same-state sweeps")
     ap.add_argument("--env-fp64", action="store_true",
@@ -419,7 +425,7 @@ def chain_mode(args):
     print(json.dumps(out))
 
 
-def accuracy_leg(args, eng, W, flux, D, qn):
+def accuracy_leg(args, eng, W, flux, D, qn, sweep_s=None, t_start=None):
     """The accuracy half of the metric, after the timed sweeps: (1) the timed engine's state,
     exported as one MPS (the regions joined by V = Lambda^-1 at every boundary, Eq. (merge)), is
     canonicalised and evaluated by an FP64 engine; (2) from that canonical state, one FP64 serial
@@ -440,6 +446,14 @@ def accuracy_leg(args, eng, W, flux, D, qn):
     e_state = f64.energy()
     b0, d0, c0 = f64.state()
     t_canon = time.perf_counter() - t0
+    if sweep_s is not None and t_start is not None:
+        # the FP64 serial sweep takes ~5x the timed mixed sweep, the mixed one ~1.3x, evaluation ~0.5x
+        projected = time.perf_counter() - t_start + 7.0 * sweep_s
+        if projected > args.time_budget_s:
+            f64.close()
+            return {"E_fp64_eval_of_timed_state": e_state, "canonicalise_and_evaluate_s": t_canon,
+                    "same_state_sweep": {"skipped": f"projected end of run {projected:.0f} s beyond the "
+                                                    f"{args.time_budget_s:.0f} s budget"}}
     torch.cuda.synchronize()
     t = time.perf_counter()
     g64 = f64.sweep(args.m, dav_tol=args.acc_tol, dav_max_iter=args.acc_iters, refine_iters=0)
@@ -847,7 +861,8 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and args.mode in ("sweeps", "steps") and not args.no_accuracy and args.precision != "fp64":
-        out["accuracy"] = accuracy_leg(args, eng, W, flux, D, qn)
+        out["accuracy"] = accuracy_leg(args, eng, W, flux, D, qn, sweep_s=ms_step / 1e3 * (
+            1.0 if args.mode == "sweeps" else 2 * (L - 1)), t_start=T_START)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample_bond = L // 2 - 1
         sample = oracle_sample(mpo, qn, mps, sample_bond)

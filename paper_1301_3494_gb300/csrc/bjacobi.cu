@@ -270,6 +270,38 @@ __device__ __forceinline__ void bj_inner(BjShared& S, int sweeps, float tol, flo
     }
 }
 
+// V(:, gcol) <- V(:, gcol) Qp for the k columns gcol of V (ld rows, `rows` of them), straight from
+// and to global memory: a thread takes whole rows (32 loads coalesced across the warp, the 32 x 32
+// products from Qp in shared memory in two halves of 16 output columns, 32 stores).
+__device__ __forceinline__ void bj_rotate_global(float* __restrict__ A, int ld, int rows, const float* __restrict__ Qp,
+                                                 const int* __restrict__ gcol, int k) {
+    for (int r = threadIdx.x; r < rows; r += BJ_THREADS) {
+        float x[BJ_K];
+#pragma unroll
+        for (int u = 0; u < BJ_K; ++u) x[u] = (u < k) ? A[(long long)gcol[u] * ld + r] : 0.f;
+#pragma unroll
+        for (int h = 0; h < BJ_K; h += 16) {
+            float acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+#pragma unroll
+            for (int u = 0; u < BJ_K; ++u) {
+#pragma unroll
+                for (int j4 = 0; j4 < 16; j4 += 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(Qp + u * BJ_QLD + h + j4);
+                    acc[j4] = fmaf(x[u], q.x, acc[j4]);
+                    acc[j4 + 1] = fmaf(x[u], q.y, acc[j4 + 1]);
+                    acc[j4 + 2] = fmaf(x[u], q.z, acc[j4 + 2]);
+                    acc[j4 + 3] = fmaf(x[u], q.w, acc[j4 + 3]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (h + j < k) A[(long long)gcol[h + j] * ld + r] = acc[j];
+        }
+    }
+}
+
 // Rotate the k columns gcol of A (ld rows, `rows` of them) by Qp, staging at most `cap` rows at
 // a time in X.
 __device__ __forceinline__ void bj_rotate_streamed(float* __restrict__ X, float* __restrict__ A, int ld, int rows,
@@ -369,11 +401,12 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
         return gram_flops;
     }
     bj_inner(S, inner_sweeps, tol, noise);
+    const float* Gf = S.G;
     // order the eigenvectors of the k real columns by decreasing eigenvalue (ties: lower index
     // first); the padding columns are never rotated and keep their positions k..31 (a real
     // column of a numerically rank-deficient pair can end with an eigenvalue rounded below zero,
     // which must not trade places with a padding column's zero)
-    if (tid < BJ_K) S.diag[tid] = S.G[tid * BJ_LD + tid];
+    if (tid < BJ_K) S.diag[tid] = Gf[tid * BJ_LD + tid];
     __syncthreads();
     if (tid < BJ_K) {
         const float d = S.diag[tid];
@@ -408,7 +441,8 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
     } else {
         bj_rotate_streamed(XW, W + s.w_off, s.p, s.p, cap, Qp, S.gcol, k);
     }
-    bj_rotate_streamed(XW, V + s.v_off, s.n, s.n, cap, Qp, S.gcol, k);
+    bj_rotate_global(V + s.v_off, s.n, s.n, Qp, S.gcol, k);
+    __syncthreads();
     return -(gram_flops + rot_flops);
 }
 
