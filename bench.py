@@ -31,7 +31,7 @@ import workloads as wl  # noqa: E402
 
 METRIC = "H_eff matvec TFLOP/s & sweep s, 24x8 m=2000; mixed vs FP64 GPU at 1e-5 dE/E"
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (per GPU)
-FP64_PEAK_TFLOPS = 1.25                 # nominal FP64 rate of a GB300
+
 
 
 T_START = time.perf_counter()
@@ -775,10 +775,12 @@ def main():
     # roofline of the matvec GEMM (the metric's kernel) and of the block-Jacobi SVD kernel; the
     # "roofline" key carries whichever of the two took more device time in the timed steps
     pk, pk_kind = peaks()
+    rates = {"fp64_fma": pd.probe(0), "fp32_fma": pd.probe(1), "bf16_tc_gemm_8192": pd.probe(2),
+             "tf32_tc_gemm_8192": pd.probe(3)}
     if args.precision == "fp64":
         g_ms, g_fl, g_n = prof["f64_gemm_ms"], prof["f64_gemm_flops"], prof["f64_gemm_launches"]
-        peak, bound = FP64_PEAK_TFLOPS, "alu"
-        peak_note = "nominal FP64 rate of a GB300 (1.25 TFLOP/s)"
+        peak, bound = rates["fp64_fma"], "alu"
+        peak_note = "measured FP64 FMA rate (dmrg_probe kind 0: eight independent DFMA chains per thread)"
         if args.fp64_emulation:
             gemm_kernel = ("k_oz_split + k_tc_gemm (bf16 slices) + k_oz_combine: every FP64 grouped GEMM of the "
                            "step, emulated")
@@ -799,8 +801,7 @@ def main():
                "launches": g_n, "flops_per_launch": g_fl / max(g_n, 1), "device_ms": g_ms, "peak_source": peak_note}
     roof = roof_mv
     if prof["svd_block_calls"] > 0:
-        sm_max = clocks.get("sm_max_mhz") or 2070.0
-        p32 = fp32_peak_tflops(sm_max)
+        p32 = rates["fp32_fma"]
         b_ms, b_fl, b_n = prof["svd_block_ms"], prof["svd_block_flops"], prof["svd_block_calls"]
         a32 = b_fl / (b_ms * 1e-3) / 1e12 if b_ms > 0 else 0.0
         trs = ncu_traffic("bjacobi_svd_traffic")
@@ -808,7 +809,8 @@ def main():
                     "traffic": trs["bytes_per_launch"] if trs and trs.get("workload") == workload_name else None,
                     "kernel": "k_bjacobi_coop (FP32 block-Jacobi SVD, one launch per split)", "launches": b_n,
                     "flops_per_launch": b_fl / b_n, "device_ms": b_ms,
-                    "peak_source": f"FP32 FMA rate from unit counts: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"}
+                    "peak_source": ("measured FP32 FMA rate (dmrg_probe kind 1: eight independent FFMA chains per "
+                                    f"thread); unit-count rate {fp32_peak_tflops(2070.0):.1f} TFLOP/s at 2070 MHz")}
         if b_ms > g_ms:
             roof = roof_svd
             roof_other = roof_mv
@@ -858,6 +860,7 @@ def main():
         "env_update_ms_per_step": ((prof["env_gemm_ms"] if env64 else prof["f32_gemm_ms"]) / args.steps
                                    if args.precision != "fp64" else None),
         "gpu_launches": prof["launches"],
+        "measured_rates_tflops": dict(rates, source="dmrg_probe (the library's own probe kernels), CUDA events"),
         "clocks": clocks,
     }
     if rank == 0 and args.mode in ("sweeps", "steps") and not args.no_accuracy and args.precision != "fp64":

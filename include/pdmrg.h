@@ -325,6 +325,14 @@ void dmrg_profile_reset(void);
 /* Synchronises the device, then copies the counters. */
 dmrg_status dmrg_profile_read(dmrg_profile* out);
 
+/* Throughput probes (the library's own kernels, timed with CUDA events on `stream`), for roofline
+ * denominators: kind 0 = FP64 FMA rate of the SMs (eight independent DFMA chains per thread),
+ * 1 = FP32 FMA rate (the same with FFMA), 2 = this library's tcgen05 grouped GEMM on one dense
+ * 8192^3 bf16 problem (FP32 accumulation), 3 = the same in tf32.  *tflops_out in TFLOP/s.  The
+ * GEMM probes allocate about 0.8 GB for their operands while they run.  Kinds 2-3 without sm_103
+ * tensor cores: DMRG_ERR_STATE.  Synchronises the stream.  No counterpart in the paper. */
+dmrg_status dmrg_probe(int kind, double* tflops_out, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Operation API: single steps on caller-provided device buffers (used for element-wise
  * parity tests and micro-benchmarks).  Layouts are the packed layouts above.

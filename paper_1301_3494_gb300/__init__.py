@@ -172,6 +172,14 @@ def profile_read():
     return p.as_dict()
 
 
+def probe(kind, stream=0):
+    """Measured throughput in TFLOP/s (dmrg_probe): 0 FP64 FMA, 1 FP32 FMA, 2 tcgen05 bf16 GEMM 8192^3,
+    3 tcgen05 tf32 GEMM 8192^3."""
+    v = C.c_double(0.0)
+    _check(lib().dmrg_probe(int(kind), C.byref(v), C.c_void_p(stream)))
+    return v.value
+
+
 def status_string(s):
     return lib().dmrg_status_string(int(s)).decode()
 

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "grid_sync.cuh"
@@ -125,40 +126,63 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GProb* __restrict__ pro
 // ------------------------------------------------------------------------------------------
 // Block copies, MPO channel mixing, diagonal
 // ------------------------------------------------------------------------------------------
+// Arithmetic of an element-wise kernel: FP64 when it writes FP64, else FP32 (an FP32 or bf16 output
+// cannot hold more; the FP64 pipe of this part is 1/64 of the FP32 one and would otherwise bound
+// these memory-bound kernels).
+template <class Tin, class Tout>
+using ew_t = typename std::conditional<std::is_same<Tout, double>::value, double, float>::type;
+template <class A, class T>
+__device__ __forceinline__ A to_a(T x) { return (A)x; }
+template <>
+__device__ __forceinline__ float to_a<float, __nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ double to_a<double, __nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+template <class T, class A>
+__device__ __forceinline__ T from_a(A v) { return (T)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_a<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_a<__nv_bfloat16, double>(double v) { return __float2bfloat16_rn((float)v); }
+
+// Element indices stay below 2^31 within a job (chunk starts are 32-bit), so the row/column split
+// uses 32-bit division.
 template <class Tin, class Tout>
 __global__ void k_copy(const CopyJob* __restrict__ jobs, const int2* __restrict__ chunks, const Tin* __restrict__ src,
                        Tout* __restrict__ dst) {
+    using A = ew_t<Tin, Tout>;
     const int2 ch = chunks[blockIdx.x];
     const CopyJob j = jobs[ch.x];
     const int w = j.cols > j.zero_to ? j.cols : j.zero_to;
     const long long total = (long long)j.rows * w;
-    const long long end = min(total, (long long)ch.y + CHUNK);
-    for (long long e = (long long)ch.y + threadIdx.x; e < end; e += blockDim.x) {
-        int r = (int)(e / w), c = (int)(e % w);
-        double v = 0.0;
-        if (c < j.cols) v = j.scale * to_d(src[j.src + (long long)r * j.srs + (long long)c * j.scs]);
-        dst[j.dst + (long long)r * j.drs + (long long)c * j.dcs] = from_d<Tout>(v);
+    const int end = (int)min(total, (long long)ch.y + CHUNK);
+    const A scale = (A)j.scale;
+    for (int e = ch.y + (int)threadIdx.x; e < end; e += blockDim.x) {
+        const int r = e / w, c = e - r * w;
+        A v = A(0);
+        if (c < j.cols) v = scale * to_a<A>(src[j.src + (long long)r * j.srs + (long long)c * j.scs]);
+        dst[j.dst + (long long)r * j.drs + (long long)c * j.dcs] = from_a<Tout>(v);
     }
 }
 
 template <class Tin, class Tout>
 __global__ void k_mix(const MixJob* __restrict__ jobs, const int2* __restrict__ chunks, const MixTerm* __restrict__ terms,
                       const Tin* __restrict__ in, Tout* __restrict__ out) {
+    using A = ew_t<Tin, Tout>;
     const int2 ch = chunks[blockIdx.x];
     const MixJob j = jobs[ch.x];
     const int w = j.cols > j.zero_to ? j.cols : j.zero_to;
     const long long total = (long long)j.rows * w;
-    const long long end = min(total, (long long)ch.y + CHUNK);
-    for (long long e = (long long)ch.y + threadIdx.x; e < end; e += blockDim.x) {
-        int r = (int)(e / w), c = (int)(e % w);
-        double v = 0.0;
+    const int end = (int)min(total, (long long)ch.y + CHUNK);
+    for (int e = ch.y + (int)threadIdx.x; e < end; e += blockDim.x) {
+        const int r = e / w, c = e - r * w;
+        A v = A(0);
         if (c < j.cols) {
             for (int t = 0; t < j.nt; ++t) {
                 const MixTerm tm = terms[j.t0 + t];
-                v += tm.coef * to_d(in[tm.src + (long long)r * tm.ld + c]);
+                v += (A)tm.coef * to_a<A>(in[tm.src + (long long)r * tm.ld + c]);
             }
         }
-        out[j.dst + (long long)r * j.ldo + c] = from_d<Tout>(v);
+        out[j.dst + (long long)r * j.ldo + c] = from_a<Tout>(v);
     }
 }
 
