@@ -1164,7 +1164,68 @@ void col_copy(const std::vector<ColJob>& jobs, const double* src, double* dst, c
 // FP64 one-sided Jacobi SVD of the column-major matrices W_s (p_s x n_s, n_s <= p_s) at ss[s].w_off
 // of W (overwritten by U_s Sigma_s).  Fills v_off / s_off / npad / pair0 of ss; V receives V_s,
 // sig the column norms and ord their descending order; dsecs the device copy of ss.
-void jacobi64(std::vector<SvdSec>& ss, double* W, DBuf& dsecs, DBuf& dV, DBuf& dsig, DBuf& dord, cudaStream_t st) {
+// FP32 block Jacobi (one task per block pair, n / 16 - 1 rounds per sweep) of the batch ss: W (p x n
+// at w_off), rotations accumulated into V (n x n at v_off, initialised by the caller); rot: sweep
+// histogram (max_sweeps + 1 ints, zeroed), bar: 3 zeroed barrier words, err: error word.
+void block_jacobi32(const std::vector<SvdSec>& ss, const SvdSec* dsecs, float* W, float* V, int max_rows, int max_n,
+                    int max_sweeps, int* rot, unsigned* bar, unsigned* err, unsigned long long* flops, cudaStream_t st) {
+    const int nsec = (int)ss.size();
+    // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it
+    const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)max_rows));
+    std::vector<BjSec> bs(nsec);
+    std::vector<int> task_sec;
+    int nrounds = 0;
+    for (int s = 0; s < nsec; ++s) {
+        BjSec b{};
+        b.nb = (ss[s].n + 15) / 16;
+        b.nbp = b.nb + (b.nb & 1);
+        b.task0 = (int)task_sec.size();
+        b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
+        for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
+        if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
+        bs[s] = b;
+    }
+    DBuf dbs, dts, dgmax;
+    upload(dbs, bs, st);
+    upload(dts, task_sec, st);
+    dgmax.ensure(std::max(1, nsec) * 4, st);
+    PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
+    PD_CK(cudaMemsetAsync(flops, 0, 8, st));
+    launch_bjacobi(dsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, max_n, 40, 2, W, V, tol,
+                   8.0f * FLT_EPSILON, dgmax.as<float>(), rot, rot + max_sweeps, bar, err, flops, st);
+}
+
+// Preconditioning of an FP64 one-sided Jacobi SVD of the batch ss (W FP64, p x n at w_off): the FP32
+// block Jacobi on an FP32 copy, its rotations orthonormalised in FP64 (Newton-Schulz) into V
+// (n x n at v_off), and W <- W V in FP64.  The FP64 Jacobi then starts from V with columns that are
+// orthogonal to FP32 accuracy, so its sweeps converge in the quadratic regime.
+void fp64_precondition(const std::vector<SvdSec>& ss, const SvdSec* dsecs, DBuf& dW, double* V, long long woff,
+                       long long voff, int maxp, int maxn, unsigned* bar, unsigned* err, cudaStream_t st) {
+    const int max_sweeps = 60;
+    DBuf w32, v32, rot32, fl, dW1;
+    w32.ensure(woff * 4, st);
+    v32.ensure(std::max<long long>(1, voff) * 4, st);
+    rot32.ensure((max_sweeps + 1) * 4, st);
+    fl.ensure(8, st);
+    PD_CK(cudaMemsetAsync(rot32.p, 0, (max_sweeps + 1) * 4, st));
+    PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+    convert_flat(dW.p, Num::F64, w32.p, Num::F32, woff, st);
+    launch_svd_init_v<float>(dsecs, (int)ss.size(), maxn, v32.as<float>(), st);
+    block_jacobi32(ss, dsecs, w32.as<float>(), v32.as<float>(), maxp, maxn, max_sweeps, rot32.as<int>(), bar, err,
+                   fl.as<unsigned long long>(), st);
+    convert_flat(v32.p, Num::F32, V, Num::F64, voff, st);
+    orthonormalize_square(ss, V, st);
+    GemmBatch gwq;
+    for (const auto& x : ss)
+        if (x.n > 0)   // W1(r, c) = sum_u W(r, u) V(u, c)
+            gwq.add(x.p, x.n, x.w_off, 1, x.p, x.n, 1, 1, x.p, {GSeg{x.w_off, x.v_off, x.n, 0}});
+    dW1.ensure(woff * 8, st);
+    run_gemm64(gwq, dW.as<double>(), V, dW1.as<double>(), st);
+    PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+    dW = std::move(dW1);
+}
+
+void jacobi64(std::vector<SvdSec>& ss, DBuf& dWbuf, DBuf& dsecs, DBuf& dV, DBuf& dsig, DBuf& dord, cudaStream_t st) {
     const int nsec = (int)ss.size();
     std::vector<int> pair_sec;
     long long voff = 0, soff = 0;
@@ -1194,7 +1255,12 @@ void jacobi64(std::vector<SvdSec>& ss, double* W, DBuf& dsecs, DBuf& dV, DBuf& d
     PD_CK(cudaMemsetAsync(drot.p, 0, (max_sweeps + 1) * 4, st));
     PD_CK(cudaMemsetAsync(dbar.p, 0, 4 * sizeof(unsigned), st));
     unsigned* bar = dbar.as<unsigned>();
-    launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
+    const long long woff = ss.empty() ? 0 : ss.back().w_off + (long long)ss.back().p * ss.back().n;
+    if (g_svd_qr && woff > 0)
+        fp64_precondition(ss, dsecs.as<SvdSec>(), dWbuf, dV.as<double>(), woff, voff, maxp, maxn, bar, bar + 3, st);
+    else
+        launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
+    double* W = dWbuf.as<double>();
     const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
     launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), (int)pair_sec.size(), maxnpad, max_sweeps, W,
                           dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(), drot.as<int>() + max_sweeps, bar, bar + 3,
@@ -1286,7 +1352,7 @@ void accurate_refine(const std::vector<SvdSec>& ss, const SvdSec* dsecs, double*
     DBuf dXW, dXsecs, dXV, dXsig, dXord;
     dXW.ensure(nx * 8, st);
     PD_CK(cudaMemcpyAsync(dXW.p, dX.p, nx * 8, cudaMemcpyDeviceToDevice, st));
-    jacobi64(xs, dXW.as<double>(), dXsecs, dXV, dXsig, dXord, st);
+    jacobi64(xs, dXW, dXsecs, dXV, dXsig, dXord, st);
     accurate_refine(xs, dXsecs.as<SvdSec>(), dXW.as<double>(), dXV.as<double>(), dXsig.as<double>(),
                     dXord.as<int>(), dX.as<double>(), depth + 1, st);
     std::vector<int> hxo(nx > 0 ? (size_t)std::max<long long>(1, xs.back().s_off + xs.back().n) : 1);
@@ -1432,34 +1498,6 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     const bool use_qr = qp.ok && !xs.empty();
     const SvdSec* jsecs = use_qr ? dxsecs.as<SvdSec>() : dsecs.as<SvdSec>();
     const int jmaxp = use_qr ? maxn : maxp;
-    // FP32 block Jacobi (one task per block pair, n / 16 - 1 rounds per sweep) of the matrices
-    // secs_d (p x n at w_off of JW, rotations accumulated at v_off of JV); rot: sweep histogram.
-    auto block_jacobi32 = [&](const SvdSec* secs_d, float* JW, float* JV, int max_rows, int* rot) {
-        // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it
-        const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)max_rows));
-        std::vector<BjSec> bs(nsec);
-        std::vector<int> task_sec;
-        int nrounds = 0;
-        for (int s = 0; s < nsec; ++s) {
-            BjSec b{};
-            b.nb = (ss[s].n + 15) / 16;
-            b.nbp = b.nb + (b.nb & 1);
-            b.task0 = (int)task_sec.size();
-            b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
-            for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
-            if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
-            bs[s] = b;
-        }
-        DBuf dbs, dts, dgmax;
-        upload(dbs, bs, st);
-        upload(dts, task_sec, st);
-        dgmax.ensure(std::max(1, nsec) * 4, st);
-        PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
-        PD_CK(cudaMemsetAsync(dflops.p, 0, 8, st));
-        launch_bjacobi(secs_d, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, maxn, 40, 2, JW,
-                       JV, tol, 8.0f * FLT_EPSILON, dgmax.as<float>(), rot, rot + max_sweeps, bar, jerr,
-                       dflops.as<unsigned long long>(), st);
-    };
     if (fp32) {
         run_copy<double>(gather, psi, dW.p, Num::F32, st);
         float* JW = dW.as<float>();
@@ -1472,7 +1510,8 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         }
         launch_svd_init_v<float>(jsecs, nsec, maxn, JV, st);
         // the kept factor that joins a block is re-orthonormalised in FP64 afterwards
-        block_jacobi32(jsecs, JW, JV, jmaxp, drot.as<int>());
+        block_jacobi32(use_qr ? xs : ss, jsecs, JW, JV, jmaxp, maxn, max_sweeps, drot.as<int>(), bar, jerr,
+                       dflops.as<unsigned long long>(), st);
         if (use_qr) {
             DBuf dWo;
             dWo.ensure(std::max<long long>(1, woff) * es, st);
@@ -1488,30 +1527,10 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
             PD_CK(cudaMemcpyAsync(dM.p, dW.p, woff * 8, cudaMemcpyDeviceToDevice, st));
         }
         const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
-        if (g_svd_qr && woff > 0) {
-            // FP32 block Jacobi on an FP32 copy, its rotations orthonormalised in FP64 (Newton-Schulz),
-            // W <- W Q in FP64, then the FP64 one-sided Jacobi from V = Q: the columns start
-            // orthogonal to FP32 accuracy, so the FP64 sweeps converge in the quadratic regime
-            DBuf w32, v32, rot32, dW1;
-            w32.ensure(woff * 4, st);
-            v32.ensure(std::max<long long>(1, voff) * 4, st);
-            rot32.ensure((max_sweeps + 1) * 4, st);
-            PD_CK(cudaMemsetAsync(rot32.p, 0, (max_sweeps + 1) * 4, st));
-            convert_flat(dW.p, Num::F64, w32.p, Num::F32, woff, st);
-            launch_svd_init_v<float>(dsecs.as<SvdSec>(), nsec, maxn, v32.as<float>(), st);
-            block_jacobi32(dsecs.as<SvdSec>(), w32.as<float>(), v32.as<float>(), maxp, rot32.as<int>());
-            convert_flat(v32.p, Num::F32, dV.p, Num::F64, voff, st);
-            orthonormalize_square(ss, dV.as<double>(), st);
-            GemmBatch gwq;
-            for (const auto& x : ss)
-                if (x.n > 0)   // W1(r, c) = sum_u W(r, u) Q(u, c)
-                    gwq.add(x.p, x.n, x.w_off, 1, x.p, x.n, 1, 1, x.p, {GSeg{x.w_off, x.v_off, x.n, 0}});
-            dW1.ensure(woff * 8, st);
-            run_gemm64(gwq, dW.as<double>(), dV.as<double>(), dW1.as<double>(), st);
-            dW = std::move(dW1);
-        } else {
+        if (g_svd_qr && woff > 0)
+            fp64_precondition(ss, dsecs.as<SvdSec>(), dW, dV.as<double>(), woff, voff, maxp, maxn, bar, jerr, st);
+        else
             launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
-        }
         launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), npairs, maxnpad, max_sweeps, dW.as<double>(),
                               dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(), drot.as<int>() + max_sweeps, bar, jerr,
                               st);
