@@ -861,6 +861,7 @@ def main():
                                    if args.precision != "fp64" else None),
         "gpu_launches": prof["launches"],
         "measured_rates_tflops": dict(rates, source="dmrg_probe (the library's own probe kernels), CUDA events"),
+        "gemm_autotuner": {"shape_classes_timed": prof["tune_classes"], "overruled_cost_model": prof["tune_changed"]},
         "clocks": clocks,
     }
     if rank == 0 and args.mode in ("sweeps", "steps") and not args.no_accuracy and args.precision != "fp64":

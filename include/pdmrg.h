@@ -318,6 +318,9 @@ typedef struct {
     long long emu_fallbacks;     /* emulated FP64 GEMM batches sent to the FP64 units by the scale
                                     guard (a shared operand row's scale class far above a problem's
                                     own row maximum) or by a NaN/Inf operand                     */
+    long long tune_classes;      /* tensor-core GEMM shape classes whose tile width was chosen by
+                                    timing every width (process-wide, not reset)               */
+    long long tune_changed;      /* of those, classes where the timing overruled the cost model  */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);

@@ -43,7 +43,8 @@ class Profile(C.Structure):
                 ("svd_ms", C.c_double), ("svd_block_calls", C.c_longlong), ("svd_fp64_calls", C.c_longlong),
                 ("svd_block_ms", C.c_double), ("svd_fp64_ms", C.c_double), ("svd_max_rows", C.c_longlong),
                 ("svd_fp64_fallbacks", C.c_longlong), ("svd_block_flops", C.c_double),
-                ("svd_rot_hist", C.c_longlong * 48), ("emu_fallbacks", C.c_longlong)]
+                ("svd_rot_hist", C.c_longlong * 48), ("emu_fallbacks", C.c_longlong), ("tune_classes", C.c_longlong),
+                ("tune_changed", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -9,6 +9,9 @@ namespace pd {
 // Grid-wide barrier with a time bound (the launch is cooperative, so all blocks are resident).
 // bar[0] = arrival count, bar[1] = generation, bar[2] = abort flag.  On expiry the block sets
 // ERRBIT_TIMEOUT and the abort flag, and every later barrier returns false at once.
+// Ordering: each block's thread 0 fences at GPU scope before it arrives and after it sees the new
+// generation, and the closing __syncthreads orders the block's other threads after thread 0, so
+// every load after the barrier (L1-cached or asynchronous) sees what any block wrote before it.
 static __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
     __shared__ int ok_s;
     __syncthreads();

@@ -156,7 +156,8 @@ struct GemmBatch {
     // device copies
     DBuf dprobs, dsegs, dtiles;
     int ntiles = 0;
-    int tile_m = 0, tile_n = 0;
+    int tile_m = 0, tile_n = 0;         // shape of the uploaded tile list
+    int bn_choice = 0;                  // tensor-core tile width chosen for this batch (0: not yet)
     long long a_rows = 0, b_rows = 0;   // slab extents (tensor-core path)
     int lda = 0, ldb = 0;
     std::shared_ptr<EmuPlan> emu;       // plan of the FP64-emulated execution, built on first use
@@ -186,6 +187,9 @@ void run_gemm32(GemmBatch& g, const float* A, const float* B, float* C, cudaStre
 void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B,
                  long long b_rows, int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st);
 bool tc_available();
+// Tile-width autotuner of the tensor-core GEMM: shape classes timed so far, and how many of them
+// chose a different width than the cost model.
+void tune_stats(long long* classes, long long* changed);
 // FP64-accurate execution of an FP64 batch on the bf16 tensor cores (error-free slicing, exact
 // FP32 accumulation, FP64 recombination).  Returns false, doing nothing, when the tensor cores
 // are unavailable or the batch's K is too large for exact accumulation.  Synchronises (checks

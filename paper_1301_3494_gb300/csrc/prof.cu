@@ -3,7 +3,7 @@
 #include <mutex>
 #include <vector>
 
-#include "internal.h"
+#include "plans.h"
 
 namespace pd {
 
@@ -149,6 +149,7 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->svd_block_flops = g_svd_block_flops;
     for (int i = 0; i < 48; ++i) out->svd_rot_hist[i] = g_rot_hist[i];
     out->emu_fallbacks = g_emu_fallbacks.load();
+    tune_stats(&out->tune_classes, &out->tune_changed);
     return DMRG_OK;
 }
 

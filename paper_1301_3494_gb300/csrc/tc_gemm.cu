@@ -16,7 +16,11 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "plans.h"
@@ -404,7 +408,41 @@ int pick_bn(const GemmBatch& g, int esize) {
     return bn_best;
 }
 
+// Measured tile-width autotuner.  A batch's shape class (operand and output types, and the
+// rounded logarithms of its flops (in pairs of octaves), mean N and mean padded K per problem),
+// for batches of at least 4 GFLOP, is timed once per
+// process with every tile width (CUDA events; one warm-up run, best of two); a width replaces the
+// cost model's choice when it is at least 10 % faster, and the choice is cached and used for every
+// later batch of that class.  Only batches that may run repeatedly are timed (no accumulation
+// into C, C distinct from A and B); the others use the cost model above.
+struct TuneKey {
+    int t, c, lf, ln, lk;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(t, c, lf, ln, lk) < std::tie(o.t, o.c, o.lf, o.ln, o.lk);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+std::atomic<long long> g_tune_changed{0};
+
+TuneKey tune_key(const GemmBatch& g, Num t, Num cnum) {
+    double n = 0.0, k = 0.0;
+    for (const auto& p : g.probs) {
+        n += p.N;
+        for (int s = 0; s < p.nseg; ++s) k += (double)((g.segs[p.seg0 + s].K + 63) / 64) * 64;
+    }
+    const double np = (double)g.probs.size();
+    auto lg = [](double x) { return (int)std::lround(std::log2(std::max(1.0, x))); };
+    return {(int)t, (int)cnum, lg(g.flops) / 2, lg(n / np), lg(k / np)};
+}
+
 }  // namespace
+
+void tune_stats(long long* classes, long long* changed) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *classes = (long long)g_tune.size();
+    *changed = g_tune_changed.load();
+}
 
 bool tc_available() {
     int dev = 0, major = 0, minor = 0;
@@ -414,15 +452,10 @@ bool tc_available() {
     return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B, long long b_rows,
-                 int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st) {
-    if (g.empty()) return;
-    PD_REQUIRE(t == Num::BF16 || t == Num::F32, DMRG_ERR_ARG, "tensor-core operands must be bf16 or fp32");
-    PD_REQUIRE(err != nullptr, DMRG_ERR_ARG, "tensor-core GEMM needs a device error word");
-    for (const auto& p : g.probs)
-        PD_REQUIRE(p.sak == 1 && p.sbk == 1 && p.sam == lda && p.sbn == ldb && p.scm == 1, DMRG_ERR_ARG,
-                   "tensor-core GEMM needs K-major slabs with uniform leading dimensions");
-    const int bn = g.tile_n ? g.tile_n : pick_bn(g, (int)num_size(t));
+namespace {
+// One launch of the batch with tile width bn (its tile list uploaded for that width).
+void launch_bn(GemmBatch& g, int bn, Num t, const void* A, long long a_rows, int lda, const void* B, long long b_rows,
+               int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st) {
     g.upload_tiles(BM, bn, st);
     const CUtensorMap ma = make_map(t, A, a_rows, lda, BM);
     const CUtensorMap mb = make_map(t, B, b_rows, ldb, bn);
@@ -441,6 +474,74 @@ void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, 
         if (bf) PD_TC(0, 64, 8); else PD_TC(1, 64, 8);
     }
 #undef PD_TC
+}
+}  // namespace
+
+void run_gemm_tc(GemmBatch& g, Num t, const void* A, long long a_rows, int lda, const void* B, long long b_rows,
+                 int ldb, void* C, Num cnum, unsigned* err, cudaStream_t st) {
+    if (g.empty()) return;
+    PD_REQUIRE(t == Num::BF16 || t == Num::F32, DMRG_ERR_ARG, "tensor-core operands must be bf16 or fp32");
+    PD_REQUIRE(err != nullptr, DMRG_ERR_ARG, "tensor-core GEMM needs a device error word");
+    for (const auto& p : g.probs)
+        PD_REQUIRE(p.sak == 1 && p.sbk == 1 && p.sam == lda && p.sbn == ldb && p.scm == 1, DMRG_ERR_ARG,
+                   "tensor-core GEMM needs K-major slabs with uniform leading dimensions");
+    int bn = g.bn_choice;
+    if (!bn) {
+        const int model = pick_bn(g, (int)num_size(t));
+        // small batches: timing noise exceeds any difference between widths
+        bool repeatable = C != A && C != B && g.flops >= 4e9;
+        for (const auto& p : g.probs) repeatable = repeatable && !p.accumulate;
+        const TuneKey key = tune_key(g, t, cnum);
+        int cached = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) cached = it->second;
+        }
+        if (cached) {
+            bn = cached;
+        } else if (repeatable) {
+            float best = -1.f;
+            int best_bn = model;
+            const int saved = g_prof_class;
+            g_prof_class = PROF_NONE;   // trial runs are not tallied
+            cudaEvent_t e0, e1;
+            PD_CK(cudaEventCreate(&e0));
+            PD_CK(cudaEventCreate(&e1));
+            float model_ms = -1.f;
+            for (int cand : {256, 128, 64}) {
+                // one untimed run (tile list, descriptors, caches), then the best of two timed runs
+                launch_bn(g, cand, t, A, a_rows, lda, B, b_rows, ldb, C, cnum, err, st);
+                float ms = -1.f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    PD_CK(cudaEventRecord(e0, st));
+                    launch_bn(g, cand, t, A, a_rows, lda, B, b_rows, ldb, C, cnum, err, st);
+                    PD_CK(cudaEventRecord(e1, st));
+                    PD_CK(cudaEventSynchronize(e1));
+                    float m = 0.f;
+                    PD_CK(cudaEventElapsedTime(&m, e0, e1));
+                    if (ms < 0.f || m < ms) ms = m;
+                }
+                if (cand == model) model_ms = ms;
+                if (best < 0.f || ms < best) { best = ms; best_bn = cand; }
+            }
+            // keep the cost model's width unless a measured one is clearly faster (timing noise)
+            if (model_ms >= 0.f && best > 0.9f * model_ms) best_bn = model;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            g_prof_class = saved;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune[key] = best_bn;
+            }
+            if (best_bn != model) g_tune_changed.fetch_add(1);
+            bn = best_bn;
+        } else {
+            bn = model;
+        }
+        g.bn_choice = bn;
+    }
+    launch_bn(g, bn, t, A, a_rows, lda, B, b_rows, ldb, C, cnum, err, st);
 }
 
 }  // namespace pd
