@@ -105,10 +105,14 @@ def parse():
                     help="accuracy: extra same-state sweeps, comma-separated precision:refine_iters[:svd64][:davN] "
                          "(e.g. tf32:6, bf16:12:dav1)")
     ap.add_argument("--regions", type=int, default=4)
-    ap.add_argument("--concurrent-regions", action="store_true",
-                    help="sweeps: one host thread and stream per region, overlapping on the GPU (default: the "
-                         "regions run one after another, each with the whole GPU)")
+    ap.add_argument("--region-schedule", choices=list(SCHEDULES), default="lockstep",
+                    help="sweeps: concurrent = one host thread and stream per region, overlapping on the GPU; "
+                         "serial = the regions one after another, each with the whole GPU; lockstep = every "
+                         "region's t-th bond step together, their FP32 splits in one grouped Jacobi launch")
     return ap.parse_args()
+
+
+SCHEDULES = {"concurrent": 0, "serial": 1, "lockstep": 2}   # dmrg_sweep_params.serial_regions
 
 
 def op_mode(args, mpo, qn, mps, center):
@@ -402,7 +406,7 @@ def chain_mode(args):
         refine = next((int(o[1:]) for o in opts[1:] if o.startswith("r") and o[1:].isdigit()), 6)
         dav_it = next((int(o[1:]) for o in opts[1:] if o.startswith("d") and o[1:].isdigit()), 12)
         dav = dict(dav_tol=0.0 if "tz" in opts else 1e-9, dav_max_iter=dav_it,
-                   refine_iters=0 if prec == "fp64" else refine, serial_regions=1)
+                   refine_iters=0 if prec == "fp64" else refine, serial_regions=SCHEDULES[args.region_schedule])
         t0 = time.perf_counter()
         eng.setup_regions(args.regions, args.chain_warmup, ramp[0], **dav)
         t_setup = time.perf_counter() - t0
@@ -734,7 +738,7 @@ def main():
     # a fixed number of Davidson steps: tensor-core iterations, then an FP32-accurate refinement
     dav = dict(dav_tol=0.0, dav_max_iter=args.dav_iters, refine_iters=args.refine_iters)
     if args.mode == "sweeps":
-        dav["serial_regions"] = 0 if args.concurrent_regions else 1
+        dav["serial_regions"] = SCHEDULES[args.region_schedule]
         eng.setup_regions(args.regions, 0, args.m, **dav)
         run_step = lambda: eng.sweep(args.m, **dav)
     else:
@@ -827,8 +831,7 @@ def main():
                    "m": args.m, "sectors_at_centre": len(mps.bonds[L // 2]), "step": args.mode,
                    "dav_iters": args.dav_iters, "refine_iters": args.refine_iters, "kmax": args.kmax,
                    "precision": args.precision, "regions": args.regions if args.mode == "sweeps" else 1,
-                   "region_schedule": (("concurrent" if args.concurrent_regions else "serial")
-                                       if args.mode == "sweeps" else None),
+                   "region_schedule": args.region_schedule if args.mode == "sweeps" else None,
                    "l2": "inputs larger than L2 (environments and intermediates > 129 MB)",
                    "fp64_gemm": "emulated on bf16 tensor cores" if emu else "FP64 units",
                    "environments": "FP64" if (env64 or not mixed) else "FP32",
@@ -851,7 +854,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": ctypes.sizeof(pd.SweepParams),
                 "d2h_bytes_per_step": ctypes.sizeof(pd.SweepStats)},
-        "svd": {"calls": prof["svd_calls"], "sweeps_per_call": prof["svd_sweeps"] / max(1, prof["svd_calls"]),
+        "svd": {"calls": prof["svd_calls"], "bonds": prof["svd_bonds"], "sweeps_per_call": prof["svd_sweeps"] / max(1, prof["svd_calls"]),
                 "ms_per_call": prof["svd_ms"] / max(1, prof["svd_calls"]),
                 "block_calls": prof["svd_block_calls"], "block_ms": prof["svd_block_ms"],
                 "fp64_calls": prof["svd_fp64_calls"], "fp64_ms": prof["svd_fp64_ms"],

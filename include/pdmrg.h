@@ -133,7 +133,12 @@ typedef struct {
                                regions' work overlapping on the GPU; 1 = the calling thread
                                runs the regions one after another (each gets the whole GPU;
                                the same results, since regions are independent between
-                               merges)                                                        */
+                               merges); 2 = lockstep: the calling thread takes every region's
+                               t-th bond step together -- Davidson region by region, then the
+                               FP32 splits of all regions as one batch (one grouped Jacobi
+                               launch, as dmrg_svd_split_batch), then each region's gauge move
+                               and environment update; the results of 1 up to the rounding
+                               of the FP32 splits                                             */
 } dmrg_sweep_params;
 
 typedef struct {
@@ -304,7 +309,8 @@ typedef struct {
     long long f32_gemm_launches; /* FP32 SIMT grouped-GEMM launches (mixed-mode environments)   */
     double f32_gemm_ms;
     double f32_gemm_flops;
-    long long svd_calls;         /* block-sparse SVDs (one per two-site split)                  */
+    long long svd_calls;         /* block-sparse SVD passes (one per split, or one per batch of
+                                    splits of several regions' bonds run together)               */
     long long svd_sweeps;        /* Jacobi sweeps they ran in total                             */
     double svd_ms;               /* device time of their Jacobi kernels                         */
     long long svd_block_calls;   /* of those, FP32 splits run by the block Jacobi                */
@@ -321,6 +327,7 @@ typedef struct {
     long long tune_classes;      /* tensor-core GEMM shape classes whose tile width was chosen by
                                     timing every width (process-wide, not reset)               */
     long long tune_changed;      /* of those, classes where the timing overruled the cost model  */
+    long long svd_bonds;         /* bonds split by those passes                                   */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);
@@ -420,6 +427,23 @@ dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int 
                            int accurate, double* A_dev, double* lam_dev, double* B_dev,
                            int cap, int* nm_out, int* qm_out, int* mm_out, double* trunc_out,
                            void* stream);
+
+/* The two-site splits (Eq. svd) of n_bonds bonds in one pass -- the concurrent bond steps of the
+ * real-space regions, Sec. II and Fig. 4: the charge sectors of all bonds form one batch of the
+ * Jacobi SVD (one grouped launch, which fills the GPU where a single bond's few large sectors
+ * leave most SMs idle), then truncation, lambda and the factors follow bond by bond, each bond
+ * with its own keep-m rule.  Every bond's outputs are those dmrg_svd_split returns for it alone
+ * in the same mode up to rounding: rotation thresholds are per sector, but how a sector's columns
+ * are staged (and so the rounding of its rotations) depends on the batch's largest sector.  Host
+ * arrays of n_bonds entries:
+ * bds (descriptors), psi_devs, A_devs, lam_devs, B_devs (device buffers owned by the caller and
+ * sized as for dmrg_svd_split), m_max; mode as for dmrg_svd_split (0-2, +4), the same for every
+ * bond.  Outputs: nm_out[n_bonds]; qm_out, mm_out[n_bonds * cap] (bond b's sectors from b * cap);
+ * trunc_out[n_bonds] (nullable).  n_bonds = 0 does nothing.  Synchronises the stream. */
+dmrg_status dmrg_svd_split_batch(int n_bonds, const dmrg_bond_desc* bds, const double* const* psi_devs,
+                                 const int* m_max, int mode, double* const* A_devs,
+                                 double* const* lam_devs, double* const* B_devs, int cap, int* nm_out,
+                                 int* qm_out, int* mm_out, double* trunc_out, void* stream);
 
 /* One problem of a grouped FP64 GEMM:
  *   C(m, n) (+)= alpha * sum over its segments sum_{k < K} A(m, k) B(n, k),   m < M, n < N,

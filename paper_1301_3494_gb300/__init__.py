@@ -44,7 +44,7 @@ class Profile(C.Structure):
                 ("svd_block_ms", C.c_double), ("svd_fp64_ms", C.c_double), ("svd_max_rows", C.c_longlong),
                 ("svd_fp64_fallbacks", C.c_longlong), ("svd_block_flops", C.c_double),
                 ("svd_rot_hist", C.c_longlong * 48), ("emu_fallbacks", C.c_longlong), ("tune_classes", C.c_longlong),
-                ("tune_changed", C.c_longlong)]
+                ("tune_changed", C.c_longlong), ("svd_bonds", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -146,6 +146,8 @@ def lib():
                                   _ip, vp]
         L.dmrg_svd_split.argtypes = [C.POINTER(BondDesc), vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, _ip, _ip, _ip,
                                      _dp, vp]
+        L.dmrg_svd_split_batch.argtypes = [C.c_int, C.POINTER(BondDesc), C.POINTER(vp), _ip, C.c_int, C.POINTER(vp),
+                                           C.POINTER(vp), C.POINTER(vp), C.c_int, _ip, _ip, _ip, _dp, vp]
         for name in ("dmrg_init_mpo", "dmrg_set_mps", "dmrg_setup_regions", "dmrg_sweep", "dmrg_advance",
                      "dmrg_profile_read", "dmrg_merge",
                      "dmrg_energy", "dmrg_get_bond", "dmrg_get_lambda", "dmrg_get_center", "dmrg_get_site",
@@ -153,7 +155,7 @@ def lib():
                      "dmrg_icmps_v", "dmrg_icmps_site", "dmrg_local_expectations",
                      "dmrg_heff_apply", "dmrg_heff_apply_noalloc", "dmrg_heff_backward", "dmrg_env_left",
                      "dmrg_env_right",
-                     "dmrg_svd_split", "dmrg_gemm64"):
+                     "dmrg_svd_split", "dmrg_svd_split_batch", "dmrg_gemm64"):
             getattr(L, name).restype = st
         _lib = L
     return _lib
@@ -266,6 +268,27 @@ def svd_split(bond: Bond, psi_dev, m_max, accurate, A_dev, lam_dev, B_dev, cap=4
     _check(lib().dmrg_svd_split(C.byref(bond.desc), psi_dev, int(m_max), int(accurate), A_dev, lam_dev, B_dev,
                                 cap, C.byref(nm), _ptr(qm, _ip), _ptr(mm, _ip), C.byref(tr), stream))
     return {int(q): int(m) for q, m in zip(qm[: nm.value], mm[: nm.value])}, tr.value
+
+
+def svd_split_batch(bonds, psi_devs, m_max, mode, A_devs, lam_devs, B_devs, cap=4096, stream=0):
+    """Splits of several bonds in one pass (dmrg_svd_split_batch): lists of Bond, device pointers
+    and m_max per bond, one mode for all (as svd_split).  Returns [(middle-bond sectors dict,
+    discarded weight)] per bond."""
+    n = len(bonds)
+    if n == 0:
+        return []
+    descs = (BondDesc * n)(*[b.desc for b in bonds])
+    P = C.c_void_p * n
+    nm = np.zeros(n, np.int32)
+    qm = np.zeros(n * cap, np.int32)
+    mm = np.zeros(n * cap, np.int32)
+    tr = np.zeros(n, np.float64)
+    mx = np.ascontiguousarray(m_max, np.int32)
+    _check(lib().dmrg_svd_split_batch(n, descs, P(*psi_devs), _ptr(mx, _ip), int(mode),
+                                      P(*A_devs), P(*lam_devs), P(*B_devs), cap, _ptr(nm, _ip), _ptr(qm, _ip),
+                                      _ptr(mm, _ip), _ptr(tr, _dp), stream))
+    return [({int(q): int(m) for q, m in zip(qm[b * cap: b * cap + nm[b]], mm[b * cap: b * cap + nm[b]])},
+             float(tr[b])) for b in range(n)]
 
 
 def gemm64(problems, segments, A_dev, B_dev, C_dev, mode=0, stream=0):

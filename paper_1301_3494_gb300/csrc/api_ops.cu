@@ -204,6 +204,67 @@ dmrg_status dmrg_svd_split(const dmrg_bond_desc* bd, const double* psi_dev, int 
     }
 }
 
+dmrg_status dmrg_svd_split_batch(int n_bonds, const dmrg_bond_desc* bds, const double* const* psi_devs,
+                                 const int* m_max, int mode, double* const* A_devs, double* const* lam_devs,
+                                 double* const* B_devs, int cap, int* nm_out, int* qm_out, int* mm_out,
+                                 double* trunc_out, void* stream) {
+    try {
+        PD_REQUIRE(n_bonds >= 0, DMRG_ERR_ARG, "n_bonds must be >= 0");
+        if (n_bonds == 0) return DMRG_OK;
+        PD_REQUIRE(bds && psi_devs && m_max && A_devs && lam_devs && B_devs && nm_out && qm_out && mm_out,
+                   DMRG_ERR_ARG, "null array");
+        PD_REQUIRE(mode >= 0 && mode <= 6 && mode != 3, DMRG_ERR_ARG, "mode must be 0-2, or 4-6");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int plain = mode >= 4;
+        const int acc = mode & 3;
+        const bool fp32 = acc == 2;
+        std::vector<std::vector<int>> qns(n_bonds);
+        std::vector<SplitReq> reqs(n_bonds);
+        for (int b = 0; b < n_bonds; ++b) {
+            const dmrg_bond_desc* bd = bds + b;
+            PD_REQUIRE(bd->d > 0 && bd->qn_local, DMRG_ERR_ARG, "bad bond descriptor");
+            PD_REQUIRE(psi_devs[b] && A_devs[b] && B_devs[b] && lam_devs[b], DMRG_ERR_ARG, "null buffer");
+            PD_REQUIRE(m_max[b] >= 1, DMRG_ERR_ARG, "m_max must be >= 1");
+            qns[b].assign(bd->qn_local, bd->qn_local + bd->d);
+            SplitReq& r = reqs[b];
+            r.bl = make_sec(bd->nl, bd->ql, bd->ml);
+            r.br = make_sec(bd->nr, bd->qr, bd->mr);
+            r.qn1 = &qns[b];
+            r.qn2 = &qns[b];
+            r.psi = psi_devs[b];
+            r.m_max = m_max[b];
+            r.A_out = A_devs[b];
+            r.B_out = B_devs[b];
+            r.lam_out_dev = lam_devs[b];
+        }
+        const int saved_qr = g_svd_qr;
+        g_svd_qr = plain ? 0 : 1;
+        std::vector<SplitResult> res;
+        try {
+            res = svd_split_batch(reqs, acc == 1, fp32, st);
+        } catch (...) {
+            g_svd_qr = saved_qr;
+            throw;
+        }
+        g_svd_qr = saved_qr;
+        for (int b = 0; b < n_bonds; ++b) {
+            const SplitResult& r = res[b];
+            if (fp32) orthonormalize_factor(reqs[b].bl, r.mid, qns[b], A_devs[b], true, st);
+            PD_REQUIRE(r.mid.n() <= cap, DMRG_ERR_CAPACITY, "output sector capacity too small");
+            nm_out[b] = r.mid.n();
+            for (int i = 0; i < r.mid.n(); ++i) {
+                qm_out[(long long)b * cap + i] = r.mid.q[i];
+                mm_out[(long long)b * cap + i] = r.mid.m[i];
+            }
+            if (trunc_out) trunc_out[b] = r.trunc;
+        }
+        PD_CK(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    }
+}
+
 dmrg_status dmrg_gemm64(const dmrg_gemm_problem* probs, int n_probs, const dmrg_gemm_segment* segs, int n_segs,
                         const double* A_dev, const double* B_dev, double* C_dev, int mode, int* info, void* stream) {
     try {

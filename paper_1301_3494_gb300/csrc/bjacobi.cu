@@ -453,7 +453,7 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
 __global__ void __launch_bounds__(BJ_THREADS, 1)
     k_bjacobi_round(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
                     int ntasks, int round, int sweep, int inner_sweeps, int max_p, int split, float* __restrict__ W,
-                    float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax, int* __restrict__ rot,
+                    float* __restrict__ V, float noise_c, float* __restrict__ gmax, int* __restrict__ rot,
                     unsigned long long* __restrict__ flops) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     if (sweep > 0 && *((volatile int*)&rot[sweep - 1]) == 0) return;
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
         const int si = task_sec[t];
         const SvdSec s = secs[si];
         const BjSec b = bsecs[si];
-        const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax,
+        const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, b.tol, noise_c, gmax,
                                  inner_sweeps);
         fl += fabs(r);
         if (r < 0.0 && threadIdx.x == 0) atomicAdd(&rot[sweep], 1);
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
 __global__ void __launch_bounds__(BJ_THREADS, 1)
     k_bjacobi_coop(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
                    int ntasks, int nrounds, int max_sweeps, int inner_sweeps, int max_p, int split,
-                   float* __restrict__ W, float* __restrict__ V, float tol, float noise_c, float* __restrict__ gmax,
+                   float* __restrict__ W, float* __restrict__ V, float noise_c, float* __restrict__ gmax,
                    int* __restrict__ rot, int* __restrict__ sweeps, unsigned* __restrict__ bar,
                    unsigned* __restrict__ err, unsigned long long* __restrict__ flops) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
                 const int si = task_sec[t];
                 const SvdSec s = secs[si];
                 const BjSec b = bsecs[si];
-                const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, tol, noise_c, gmax,
+                const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, b.tol, noise_c, gmax,
                                          inner_sweeps);
                 fl += fabs(r);
                 if (r < 0.0 && threadIdx.x == 0) atomicAdd(&rot[sweep], 1);
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
 int bjacobi_max_rows() { return (int)((BJ_SMEM_MAX - sizeof(BjShared)) / (BJ_LD * sizeof(float))); }
 
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
-                    int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c,
+                    int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float noise_c,
                     float* gmax, int* rot, int* sweeps, unsigned* bar, unsigned* err, unsigned long long* flops,
                     cudaStream_t st) {
     if (ntasks <= 0 || nrounds <= 0) {
@@ -563,7 +563,7 @@ void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec,
         PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
         void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&task_sec, (void*)&ntasks, (void*)&nrounds,
                         (void*)&max_sweeps, (void*)&inner_sweeps, (void*)&max_rows, (void*)&split, (void*)&W,
-                        (void*)&V, (void*)&tol, (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps,
+                        (void*)&V, (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps,
                         (void*)&bar, (void*)&err, (void*)&flops};
         PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi_coop, cblocks, BJ_THREADS, args, smem, st));
         PD_LAUNCHED();
@@ -581,7 +581,7 @@ void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec,
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
             for (int round = 0; round < nrounds; ++round) {
                 k_bjacobi_round<<<blocks, BJ_THREADS, smem, st>>>(secs, bsecs, task_sec, ntasks, round, sweep,
-                                                                   inner_sweeps, max_rows, split, W, V, tol, noise_c,
+                                                                   inner_sweeps, max_rows, split, W, V, noise_c,
                                                                    gmax, rot, flops);
                 PD_LAUNCHED();
             }

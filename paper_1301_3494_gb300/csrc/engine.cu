@@ -256,20 +256,26 @@ DavResult solve_bond(dmrg_ctx* c, Chain& ch, int j, EnvSlab& Lj, EnvSlab& Rj, DB
     return r;
 }
 
-// Split psi at bond j, store A/B/Lambda in the chain, update the environment behind the move.
-void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_max, bool accurate, StepStats& s,
-                    SplitResult* out = nullptr, bool edge = false) {
+// Mixed-precision modes split ordinary bonds by the FP32 Jacobi; FP64 at shared (accurate) bonds,
+// on edge bonds when the context asks for FP64 edge splits, and everywhere in FP64 mode.
+bool split_fp32(const dmrg_ctx* c, bool accurate, bool edge) {
+    return c->prec != DMRG_FP64 && !accurate && !c->svd_fp64 && !(edge && fp64_edge_split(c));
+}
+
+// Output buffers of the split at bond j (FP64, packed A and B blocks).
+void alloc_split(dmrg_ctx* c, const Chain& ch, int j, DBuf& A, DBuf& B) {
+    long long na, nb, nl;
+    svd_split_bounds(ch.bond[j], ch.bond[j + 2], c->qn, c->qn, &na, &nb, &nl);
+    A.ensure(std::max<long long>(1, na) * 8, ch.st);
+    B.ensure(std::max<long long>(1, nb) * 8, ch.st);
+}
+
+// After the split r of psi at bond j into A, B: store A/B/Lambda in the chain and update the
+// environment behind the move.
+void finish_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_max, bool accurate, bool fp32,
+                 SplitResult& r, DBuf& A, DBuf& B, StepStats& s) {
     cudaStream_t st = ch.st;
     const Sec bl = ch.bond[j], br = ch.bond[j + 2];
-    long long na, nb, nl;
-    svd_split_bounds(bl, br, c->qn, c->qn, &na, &nb, &nl);
-    DBuf A, B;
-    A.ensure(std::max<long long>(1, na) * 8, st);
-    B.ensure(std::max<long long>(1, nb) * 8, st);
-    // mixed-precision modes: FP32 Jacobi on ordinary bonds; FP64 at shared (accurate) bonds
-    const bool fp32 = c->prec != DMRG_FP64 && !accurate && !c->svd_fp64 && !(edge && fp64_edge_split(c));
-    SplitResult r = svd_split(bl, br, c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate, right ? 0 : 1,
-                              right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, st, fp32);
     if (fp32) {
         // the factor that joins a block must be orthonormal to FP64 accuracy; an FP32 split whose
         // kept vectors are beyond the reach of the re-orthonormalisation (FP32 rounding left
@@ -310,6 +316,17 @@ void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_
     }
     ch.site[j] = std::move(A);
     ch.site[j + 1] = std::move(B);
+}
+
+// Split psi at bond j, store A/B/Lambda in the chain, update the environment behind the move.
+void split_and_move(dmrg_ctx* c, Chain& ch, int j, bool right, DBuf& psi, int m_max, bool accurate, StepStats& s,
+                    SplitResult* out = nullptr, bool edge = false) {
+    DBuf A, B;
+    alloc_split(c, ch, j, A, B);
+    const bool fp32 = split_fp32(c, accurate, edge);
+    SplitResult r = svd_split(ch.bond[j], ch.bond[j + 2], c->qn, c->qn, psi.as<double>(), m_max, 1e-12, accurate,
+                              right ? 0 : 1, right ? 1 : 0, A.as<double>(), B.as<double>(), nullptr, ch.st, fp32);
+    finish_move(c, ch, j, right, psi, m_max, accurate, fp32, r, A, B, s);
     if (out) *out = r;
 }
 
@@ -390,9 +407,13 @@ double rayleigh_fp64(dmrg_ctx* c, Chain& ch, int j, const double* psi) {
 // ------------------------------------------------------------------------------------------
 // Regions
 // ------------------------------------------------------------------------------------------
+// Edge bonds of a region: (q-1, q) when bond q+1 is a boundary, (p, p+1) when bond p is one.
+bool edge_bond(const dmrg_ctx* c, const Chain& r, int j) {
+    return (j == r.q - 1 && r.q + 1 < c->L) || (j == r.p && r.p > 0);
+}
+
 void region_half_sweep(dmrg_ctx* c, Chain& r, bool right, const dmrg_sweep_params* p) {
-    // edge bonds: (q-1, q) when bond q+1 is a boundary, (p, p+1) when bond p is one
-    auto edge = [&](int j) { return (j == r.q - 1 && r.q + 1 < c->L) || (j == r.p && r.p > 0); };
+    auto edge = [&](int j) { return edge_bond(c, r, j); };
     if (right) {
         PD_REQUIRE(r.oc == r.p, DMRG_ERR_STATE, "region centre not at its left end");
         for (int j = r.p; j < r.q; ++j) bond_step(c, r, j, true, p, false, edge(j));
@@ -400,6 +421,80 @@ void region_half_sweep(dmrg_ctx* c, Chain& r, bool right, const dmrg_sweep_param
         PD_REQUIRE(r.oc == r.q, DMRG_ERR_STATE, "region centre not at its right end");
         for (int j = r.q - 1; j >= r.p; --j) bond_step(c, r, j, false, p, false, edge(j));
     }
+}
+
+void stream_after(cudaStream_t waiter, cudaStream_t producer);
+
+// Half sweeps of the regions ks (directions right[i]) in lockstep: at step t every region forms
+// Psi on its t-th bond and solves it, then the splits of all these bonds run as one batch per
+// precision on the context's base stream -- one Jacobi launch over the charge sectors of every
+// region's bond, which keeps the SMs busy in the late rounds where one bond's largest sectors
+// alone leave most of them idle -- and every region then finishes its own move.
+void lockstep_half(dmrg_ctx* c, const std::vector<int>& ks, const std::vector<char>& right,
+                   const dmrg_sweep_params* p) {
+    const int n = (int)ks.size();
+    int steps = 0;
+    for (int i = 0; i < n; ++i) {
+        const Chain& r = *c->reg[ks[i]];
+        PD_REQUIRE(r.oc == (right[i] ? r.p : r.q), DMRG_ERR_STATE, "region centre not at the start of its half sweep");
+        steps = std::max(steps, r.q - r.p);
+    }
+    for (int t = 0; t < steps; ++t) {
+        std::vector<DBuf> psi(n), A(n), B(n);
+        std::vector<int> js(n, -1);
+        std::vector<char> f32(n, 0);
+        for (int i = 0; i < n; ++i) {
+            Chain& r = *c->reg[ks[i]];
+            if (t >= r.q - r.p) continue;
+            const int j = right[i] ? r.p + t : r.q - 1 - t;
+            const bool edge = edge_bond(c, r, j);
+            js[i] = j;
+            form_psi(c, r, j, psi[i]);
+            StepStats& s = r.acc;
+            DavResult d = solve_bond(c, r, j, *r.Lenv[j], *r.Renv[j + 2], psi[i], p, s, nullptr, edge);
+            s.energy = d.theta;
+            s.steps++;
+            f32[i] = split_fp32(c, false, edge);
+        }
+        // one batch per split precision (FP32 block Jacobi; FP64 for edge bonds when asked for)
+        std::vector<SplitResult> res(n);
+        for (int prec32 = 1; prec32 >= 0; --prec32) {
+            std::vector<SplitReq> reqs;
+            std::vector<int> who;
+            for (int i = 0; i < n; ++i) {
+                if (js[i] < 0 || f32[i] != prec32) continue;
+                Chain& r = *c->reg[ks[i]];
+                const int j = js[i];
+                alloc_split(c, r, j, A[i], B[i]);
+                SplitReq q;
+                q.bl = r.bond[j];
+                q.br = r.bond[j + 2];
+                q.qn1 = &c->qn;
+                q.qn2 = &c->qn;
+                q.psi = psi[i].as<double>();
+                q.m_max = p->m_max;
+                q.lam_pow_left = right[i] ? 0 : 1;
+                q.lam_pow_right = right[i] ? 1 : 0;
+                q.A_out = A[i].as<double>();
+                q.B_out = B[i].as<double>();
+                reqs.push_back(q);
+                who.push_back(i);
+                stream_after(c->base, r.st);
+            }
+            if (reqs.empty()) continue;
+            std::vector<SplitResult> rb = svd_split_batch(reqs, false, prec32 != 0, c->base);
+            for (size_t q = 0; q < who.size(); ++q) {
+                res[who[q]] = std::move(rb[q]);
+                stream_after(c->reg[ks[who[q]]]->st, c->base);
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            if (js[i] < 0) continue;
+            Chain& r = *c->reg[ks[i]];
+            finish_move(c, r, js[i], right[i] != 0, psi[i], p->m_max, false, f32[i] != 0, res[i], A[i], B[i], r.acc);
+        }
+    }
+    for (int k : ks) check_err_word(c->reg[k]->err.as<unsigned>(), c->reg[k]->st);
 }
 
 // Run fn(i) for i in items on one host thread each (every region drives its own stream).
@@ -666,6 +761,10 @@ void setup_regions(dmrg_ctx* c, int R, int warmup, const dmrg_sweep_params* p) {
     // staggered start (Fig. 4): even regions (1-based) move to their right end
     std::vector<int> odd;
     for (int k = 1; k < R; k += 2) odd.push_back(k);
+    if (p->serial_regions == 2) {
+        lockstep_half(c, odd, std::vector<char>(odd.size(), 1), p);
+        return;
+    }
     parallel_items(odd, [&](int k) {
         region_half_sweep(c, *c->reg[k], true, p);
         check_err_word(c->reg[k]->err.as<unsigned>(), c->reg[k]->st);
@@ -682,6 +781,12 @@ StepStats region_sweep(dmrg_ctx* c, const dmrg_sweep_params* p) {
     for (int k = 2; k < R; k += 2) md.push_back(k);
     double e_last = 0.0;
     auto half = [&](bool first) {
+        if (p->serial_regions == 2) {
+            std::vector<char> dirs(R);
+            for (int k = 0; k < R; ++k) dirs[k] = (k % 2 == 0) == first;
+            lockstep_half(c, all, dirs, p);
+            return;
+        }
         parallel_items(all, [&](int k) {
             bool right = (k % 2 == 0) == first;
             region_half_sweep(c, *c->reg[k], right, p);

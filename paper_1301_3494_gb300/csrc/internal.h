@@ -53,7 +53,8 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops);
 // Jacobi SVD statistics (sweeps run per call), accumulated while profiling is on; kind 0: FP32
 // scalar Jacobi, 1: FP32 block Jacobi, 2: FP64; max_rows: the call's largest sector row count;
 // flops: the FP32 Gram and rotation flops of a block-Jacobi call; rot_hist: its rotations per sweep.
-void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist);
+void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist,
+              int bonds = 1);
 // An FP32 split redone in FP64 (counted always, not only while profiling).
 void prof_fallback();
 // An emulated FP64 GEMM batch sent to the FP64 units by its scale guard (counted always).
@@ -196,6 +197,8 @@ struct SvdSec {
 template <class T>
 void launch_svd_init_v(const SvdSec* secs, int nsec, int max_n, T* V, cudaStream_t st);
 // All Jacobi sweeps (until a sweep without rotation, at most max_sweeps) in one cooperative launch.
+// A pair of columns with Gram entries a, b, g is rotated when |g| > tol sqrt(p) sqrt(a b), p the
+// row count of its own sector (the rounding noise of a p-long dot product grows like sqrt(p)).
 // Pairs whose smaller column norm is below eta * |W_sector|_F are not rotated (eta = 0: all are).
 // floor2: nsec doubles of scratch (unused when eta = 0).
 // bar: 3 unsigned words of scratch for the bounded grid barrier; err: device error word.
@@ -206,12 +209,15 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
 // Block one-sided Jacobi (FP32, blocks of 16 columns) over the same sector batch.  Per sector:
 // nb = ceil(n / 16) blocks, nbp = nb rounded up to even, task0 = first task of the sector in a
 // round, ntask = tasks per round (nbp / 2; 1 when nb = 1).  task_sec[t] = sector of task t.
+// tol: the sector's relative rotation threshold (FP32 dot products of p-long columns carry about
+// eps * sqrt(p) relative noise, so it sits above that).
 struct BjSec {
     int nb, nbp, task0, ntask;
+    float tol;
 };
 int bjacobi_max_rows();
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
-                    int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float tol, float noise_c, float* gmax,
+                    int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float noise_c, float* gmax,
                     int* rot, int* sweeps, unsigned* bar, unsigned* err, unsigned long long* flops, cudaStream_t st);
 template <class T>
 void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st);

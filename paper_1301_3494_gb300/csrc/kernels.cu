@@ -468,7 +468,7 @@ __global__ void k_jacobi_coop(const SvdSec* __restrict__ secs, const int* __rest
             for (int w = gw; w < npairs; w += nw) {
                 const int si = pair_sec[w];
                 const SvdSec s = secs[si];
-                if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, floor2 ? (T)floor2[si] : T(0), lane)) mine = 1;
+                if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol * sqrt((T)s.p), floor2 ? (T)floor2[si] : T(0), lane)) mine = 1;
             }
             alive = grid_barrier(bar, gridDim.x, err);
         }
@@ -493,7 +493,7 @@ __global__ void k_jacobi_round(const SvdSec* __restrict__ secs, const int* __res
     if (w >= npairs) return;
     const int si = pair_sec[w];
     const SvdSec s = secs[si];
-    if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol, floor2 ? (T)floor2[si] : T(0), lane) && lane == 0)
+    if (jacobi_pair<T>(s, w - s.pair0, round, W, V, tol * sqrt((T)s.p), floor2 ? (T)floor2[si] : T(0), lane) && lane == 0)
         rot[sweep] = 1;
 }
 

@@ -1171,8 +1171,6 @@ void col_copy(const std::vector<ColJob>& jobs, const double* src, double* dst, c
 void block_jacobi32(const std::vector<SvdSec>& ss, const SvdSec* dsecs, float* W, float* V, int max_rows, int max_n,
                     int max_sweeps, int* rot, unsigned* bar, unsigned* err, unsigned long long* flops, cudaStream_t st) {
     const int nsec = (int)ss.size();
-    // FP32 dot products carry ~eps*sqrt(p) noise, so the rotation threshold sits above it
-    const float tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)max_rows));
     std::vector<BjSec> bs(nsec);
     std::vector<int> task_sec;
     int nrounds = 0;
@@ -1182,6 +1180,8 @@ void block_jacobi32(const std::vector<SvdSec>& ss, const SvdSec* dsecs, float* W
         b.nbp = b.nb + (b.nb & 1);
         b.task0 = (int)task_sec.size();
         b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
+        // each sector's own threshold, so a split's result does not depend on its batch
+        b.tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)std::max(1, ss[s].p)));
         for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
         if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
         bs[s] = b;
@@ -1192,7 +1192,7 @@ void block_jacobi32(const std::vector<SvdSec>& ss, const SvdSec* dsecs, float* W
     dgmax.ensure(std::max(1, nsec) * 4, st);
     PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
     PD_CK(cudaMemsetAsync(flops, 0, 8, st));
-    launch_bjacobi(dsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, max_n, 40, 2, W, V, tol,
+    launch_bjacobi(dsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, max_n, 40, 2, W, V,
                    8.0f * FLT_EPSILON, dgmax.as<float>(), rot, rot + max_sweeps, bar, err, flops, st);
 }
 
@@ -1262,7 +1262,7 @@ void jacobi64(std::vector<SvdSec>& ss, DBuf& dWbuf, DBuf& dsecs, DBuf& dV, DBuf&
     else
         launch_svd_init_v<double>(dsecs.as<SvdSec>(), nsec, maxn, dV.as<double>(), st);
     double* W = dWbuf.as<double>();
-    const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+    const double tol = 4.0 * DBL_EPSILON;
     launch_jacobi<double>(dsecs.as<SvdSec>(), nsec, dpairs.as<int>(), (int)pair_sec.size(), maxnpad, max_sweeps, W,
                           dV.as<double>(), tol, 0.0, nullptr, drot.as<int>(), drot.as<int>() + max_sweeps, bar, bar + 3,
                           st);
@@ -1401,60 +1401,80 @@ void accurate_refine(const std::vector<SvdSec>& ss, const SvdSec* dsecs, double*
 
 }  // namespace
 
-SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
-                      const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
-                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st,
-                      bool fp32) {
+std::vector<SplitResult> svd_split_batch(const std::vector<SplitReq>& reqs, bool accurate, bool fp32, cudaStream_t st) {
     const size_t es = fp32 ? 4 : 8;
-    const PsiLayout P = psi_layout2(bl, br, qn1, qn2);
-    const std::vector<int>& qn = qn1;
-    // sector layout: rows (i, s1) sorted, cols (s2, k) sorted, per middle charge
-    auto secs = split_sectors(P, bl, br, qn1);
-    std::vector<SecInfo*> order_secs;
-    for (auto& kv : secs) order_secs.push_back(&kv.second);
-    const int nsec = (int)order_secs.size();
-    std::vector<SvdSec> ss(nsec);
+    const int nreq = (int)reqs.size();
+    // per bond: sector layout (rows (i, s1) sorted, cols (s2, k) sorted, per middle charge); the
+    // sectors of all bonds are numbered consecutively and packed into joint W / V / sigma buffers
+    struct Front {
+        PsiLayout P;
+        std::map<int, SecInfo> secs;
+        std::vector<SecInfo*> order;
+        int sec0 = 0, nsec = 0, total = 0, maxp = 1;
+        long long sbase = 0;
+    };
+    std::vector<Front> fr(nreq);
+    std::vector<SvdSec> ss;
     std::vector<int> pair_sec;
     long long woff = 0, voff = 0, soff = 0;
-    int maxn = 0, maxnpad = 0, maxp = 1;
-    for (int s = 0; s < nsec; ++s) {
-        auto& S = *order_secs[s];
-        SvdSec x{};
-        x.p = std::max(S.r, S.c);
-        x.n = std::min(S.r, S.c);
-        x.npad = x.n + (x.n & 1);
-        x.w_off = woff; x.v_off = voff; x.s_off = soff;
-        x.pair0 = (int)pair_sec.size();
-        for (int i = 0; i < x.npad / 2; ++i) pair_sec.push_back(s);
-        woff += (long long)x.p * x.n;
-        voff += (long long)x.n * x.n;
-        soff += x.n;
-        maxn = std::max(maxn, x.n);
-        maxp = std::max(maxp, x.p);
-        maxnpad = std::max(maxnpad, x.npad);
-        ss[s] = x;
-    }
-    const int total = (int)soff;
-    // gather Psi blocks into W
-    CopyList gather;
-    for (const auto& b : P.blk) {
-        int qm = bl.q[b.i] + qn[b.s1];
-        int s = (int)(std::find_if(order_secs.begin(), order_secs.end(), [&](SecInfo* x) { return x->qm == qm; }) - order_secs.begin());
-        const auto& S = *order_secs[s];
-        int r0 = S.roff.at({b.i, b.s1}), c0 = S.coff.at({b.s2, b.k});
-        CopyJob j{};
-        j.src = b.off; j.rows = b.rows; j.cols = b.cols; j.srs = b.cols; j.scs = 1; j.zero_to = 0; j.scale = 1.0;
-        if (S.r >= S.c) {   // W = M, column-major r x c
-            j.dst = ss[s].w_off + (long long)c0 * S.r + r0; j.drs = 1; j.dcs = S.r;
-        } else {            // W = M^T, column-major c x r
-            j.dst = ss[s].w_off + (long long)r0 * S.c + c0; j.drs = S.c; j.dcs = 1;
+    int maxn = 0, maxnpad = 0, maxp = 1, max_total = 1, max_nsec = 1;
+    for (int q = 0; q < nreq; ++q) {
+        const SplitReq& R = reqs[q];
+        Front& F = fr[q];
+        F.P = psi_layout2(R.bl, R.br, *R.qn1, *R.qn2);
+        F.secs = split_sectors(F.P, R.bl, R.br, *R.qn1);
+        for (auto& kv : F.secs) F.order.push_back(&kv.second);
+        F.sec0 = (int)ss.size();
+        F.nsec = (int)F.order.size();
+        F.sbase = soff;
+        for (int s = 0; s < F.nsec; ++s) {
+            const auto& S = *F.order[s];
+            SvdSec x{};
+            x.p = std::max(S.r, S.c);
+            x.n = std::min(S.r, S.c);
+            x.npad = x.n + (x.n & 1);
+            x.w_off = woff; x.v_off = voff; x.s_off = soff;
+            x.pair0 = (int)pair_sec.size();
+            for (int i = 0; i < x.npad / 2; ++i) pair_sec.push_back(F.sec0 + s);
+            woff += (long long)x.p * x.n;
+            voff += (long long)x.n * x.n;
+            soff += x.n;
+            maxn = std::max(maxn, x.n);
+            F.maxp = std::max(F.maxp, x.p);
+            maxnpad = std::max(maxnpad, x.npad);
+            ss.push_back(x);
         }
-        gather.add(j);
+        F.total = (int)(soff - F.sbase);
+        maxp = std::max(maxp, F.maxp);
+        max_total = std::max(max_total, F.total);
+        max_nsec = std::max(max_nsec, F.nsec);
     }
-    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dfloor, dbar, dflops;
+    const int nsec = (int)ss.size();
+    // gather each bond's Psi blocks into its matrices (W = M, or M^T when M is wide; column-major)
+    std::vector<CopyList> gather(nreq);
+    for (int q = 0; q < nreq; ++q) {
+        const Front& F = fr[q];
+        const std::vector<int>& qn = *reqs[q].qn1;
+        for (const auto& b : F.P.blk) {
+            const int qm = reqs[q].bl.q[b.i] + qn[b.s1];
+            const int s = (int)(std::find_if(F.order.begin(), F.order.end(), [&](SecInfo* x) { return x->qm == qm; }) -
+                                F.order.begin());
+            const auto& S = *F.order[s];
+            const SvdSec& x = ss[F.sec0 + s];
+            const int r0 = S.roff.at({b.i, b.s1}), c0 = S.coff.at({b.s2, b.k});
+            CopyJob j{};
+            j.src = b.off; j.rows = b.rows; j.cols = b.cols; j.srs = b.cols; j.scs = 1; j.zero_to = 0; j.scale = 1.0;
+            if (S.r >= S.c) {
+                j.dst = x.w_off + (long long)c0 * S.r + r0; j.drs = 1; j.dcs = S.r;
+            } else {
+                j.dst = x.w_off + (long long)r0 * S.c + c0; j.drs = S.c; j.dcs = 1;
+            }
+            gather[q].add(j);
+        }
+    }
+    DBuf dW, dV, dsig, dord, dsecs, dpairs, drot, dkept, dwts, dbar, dflops;
     dflops.ensure(8, st);
     const int max_sweeps = 60;
-    dfloor.ensure(std::max(1, nsec) * 8, st);
     dbar.ensure(4 * sizeof(unsigned), st);     // barrier words + the error word
     PD_CK(cudaMemsetAsync(dbar.p, 0, 4 * sizeof(unsigned), st));
     unsigned* bar = dbar.as<unsigned>();
@@ -1464,11 +1484,11 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     dsig.ensure(std::max<long long>(1, soff) * 8, st);
     dord.ensure(std::max<long long>(1, soff) * 4, st);
     dkept.ensure(std::max(1, nsec) * 4, st);
-    dwts.ensure(16, st);
+    dwts.ensure(std::max(1, nreq) * 16, st);
     drot.ensure((max_sweeps + 1) * 4, st);
     upload(dsecs, ss, st);
     upload(dpairs, pair_sec, st);
-    gather.up(st);
+    for (auto& g : gather) g.up(st);
     PD_CK(cudaMemsetAsync(dW.p, 0, std::max<long long>(1, woff) * es, st));
     PD_CK(cudaMemsetAsync(drot.p, 0, (max_sweeps + 1) * 4, st));
     const int npairs = (int)pair_sec.size();
@@ -1500,7 +1520,7 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
     const SvdSec* jsecs = use_qr ? dxsecs.as<SvdSec>() : dsecs.as<SvdSec>();
     const int jmaxp = use_qr ? maxn : maxp;
     if (fp32) {
-        run_copy<double>(gather, psi, dW.p, Num::F32, st);
+        for (int q = 0; q < nreq; ++q) run_copy<double>(gather[q], reqs[q].psi, dW.p, Num::F32, st);
         float* JW = dW.as<float>();
         float* JV = dV.as<float>();
         if (use_qr) {
@@ -1521,13 +1541,13 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         }
         launch_svd_finish<float>(dsecs.as<SvdSec>(), nsec, dW.as<float>(), dsig.as<double>(), dord.as<int>(), st);
     } else {
-        run_copy<double>(gather, psi, dW.p, Num::F64, st);
+        for (int q = 0; q < nreq; ++q) run_copy<double>(gather[q], reqs[q].psi, dW.p, Num::F64, st);
         DBuf dM;
         if (accurate && woff > 0) {
             dM.ensure(woff * 8, st);
             PD_CK(cudaMemcpyAsync(dM.p, dW.p, woff * 8, cudaMemcpyDeviceToDevice, st));
         }
-        const double tol = 4.0 * DBL_EPSILON * std::sqrt((double)maxp);
+        const double tol = 4.0 * DBL_EPSILON;   // per sector: times sqrt(p)
         if (g_svd_qr && woff > 0)
             fp64_precondition(ss, dsecs.as<SvdSec>(), dW, dV.as<double>(), woff, voff, maxp, maxn, bar, jerr, st);
         else
@@ -1551,115 +1571,156 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
         PD_CK(cudaStreamSynchronize(st));
         float ms = 0.f;
         PD_CK(cudaEventElapsedTime(&ms, sv0, sv1));
-        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl, fp32 ? hist.data() : nullptr, max_sweeps);
+        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl, fp32 ? hist.data() : nullptr, max_sweeps, nreq);
         cudaEventDestroy(sv0);
         cudaEventDestroy(sv1);
     }
-    DBuf tsd, tsi;
-    tsd.ensure((size_t)(total + nsec + 1) * 8, st);
-    tsi.ensure((size_t)(3 * total + 1) * 4, st);
+    // truncation per bond (the keep-m rule runs over one bond's sectors): its sector table with
+    // sigma offsets relative to the bond's first sector, and sigma / order shifted to match
+    std::vector<SvdSec> tl = ss;
+    for (const Front& F : fr)
+        for (int s = 0; s < F.nsec; ++s) tl[F.sec0 + s].s_off -= F.sbase;
+    DBuf dtl, tsd, tsi;
+    upload(dtl, tl, st);
+    tsd.ensure((size_t)(max_total + max_nsec + 1) * 8, st);
+    tsi.ensure((size_t)(3 * max_total + 1) * 4, st);
     // an FP32 SVD reports exact zeros at ~1e-7 of the largest singular value: keep its cutoff
     // above that noise floor (the discarded weight stays below 1e-10)
-    const double cutoff = fp32 ? std::max(rel_cutoff, 1e-5) : rel_cutoff;
-    launch_truncate(dsecs.as<SvdSec>(), nsec, dsig.as<double>(), dord.as<int>(), total, m_max, cutoff, 1e-10,
-                    dkept.as<int>(), dwts.as<double>(), tsd.as<double>(), tsi.as<int>(), st);
-    std::vector<int> kept(nsec);
-    double wts[2];
+    for (int q = 0; q < nreq; ++q) {
+        const Front& F = fr[q];
+        const double cutoff = fp32 ? std::max(reqs[q].rel_cutoff, 1e-5) : reqs[q].rel_cutoff;
+        launch_truncate(dtl.as<SvdSec>() + F.sec0, F.nsec, dsig.as<double>() + F.sbase, dord.as<int>() + F.sbase,
+                        F.total, reqs[q].m_max, cutoff, 1e-10, dkept.as<int>() + F.sec0, dwts.as<double>() + 2 * q,
+                        tsd.as<double>(), tsi.as<int>(), st);
+    }
+    std::vector<int> kept(std::max(1, nsec));
+    std::vector<double> wts(2 * std::max(1, nreq));
     unsigned jerr_h = 0;
     int sweeps_h = 0;
     PD_CK(cudaMemcpyAsync(&sweeps_h, drot.as<int>() + max_sweeps, 4, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(&jerr_h, jerr, 4, cudaMemcpyDeviceToHost, st));
-    PD_CK(cudaMemcpyAsync(kept.data(), dkept.p, 4 * nsec, cudaMemcpyDeviceToHost, st));
-    PD_CK(cudaMemcpyAsync(wts, dwts.p, 16, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(kept.data(), dkept.p, 4 * std::max(1, nsec), cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(wts.data(), dwts.p, 16 * std::max(1, nreq), cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
     PD_REQUIRE(!(jerr_h & ERRBIT_TIMEOUT), DMRG_ERR_TIMEOUT, "Jacobi SVD grid barrier timed out");
-    SplitResult res;
-    res.sweeps = sweeps_h;
-    res.max_rows = maxp;
-    std::vector<int> kept_of_sec(nsec, 0);
-    for (int s = 0; s < nsec; ++s)
-        if (kept[s] > 0) {
-            res.mid.q.push_back(order_secs[s]->qm);
-            res.mid.m.push_back(kept[s]);
-            kept_of_sec[s] = kept[s];
+    std::vector<SplitResult> out(nreq);
+    std::vector<DBuf> keep_alive;
+    keep_alive.reserve(4 * nreq);
+    for (int q = 0; q < nreq; ++q) {
+        const Front& F = fr[q];
+        const SplitReq& R = reqs[q];
+        const std::vector<int>& qn1 = *R.qn1;
+        const std::vector<int>& qn2 = *R.qn2;
+        SplitResult& res = out[q];
+        res.sweeps = sweeps_h;
+        res.max_rows = F.maxp;
+        std::vector<int> kept_of_sec(F.nsec, 0);
+        for (int s = 0; s < F.nsec; ++s)
+            if (kept[F.sec0 + s] > 0) {
+                res.mid.q.push_back(F.order[s]->qm);
+                res.mid.m.push_back(kept[F.sec0 + s]);
+                kept_of_sec[s] = kept[F.sec0 + s];
+            }
+        PD_REQUIRE(res.mid.n() > 0, DMRG_ERR_NUMERIC, "SVD kept no singular value (zero wavefunction?)");
+        const double w0 = wts[2 * q], w1 = wts[2 * q + 1];
+        res.trunc = w0 > 0 ? std::max(0.0, (w0 - w1) / w0) : 0.0;
+        // scatter
+        const SiteLayout SA = site_layout(R.bl, res.mid, qn1);
+        const SiteLayout SB = site_layout(res.mid, R.br, qn2);
+        std::vector<ScatJob> ja, jb;
+        int mx = 1;
+        for (int s = 0; s < F.nsec; ++s) {
+            if (!kept_of_sec[s]) continue;
+            const auto& S = *F.order[s];
+            const SvdSec& x = ss[F.sec0 + s];
+            const int im = res.mid.find(S.qm);
+            const bool rge = S.r >= S.c;
+            for (const auto& r : S.roff) {        // A blocks (i, s1) [a][k]
+                const int ab = SA.at(r.first.first, r.first.second);
+                if (ab < 0) continue;
+                ScatJob j{};
+                j.dst = SA.blk[ab].off; j.rows = SA.blk[ab].rows; j.cols = SA.blk[ab].cols;
+                j.s_off = x.s_off; j.off0 = r.second; j.left = 1; j.lam_pow = R.lam_pow_left;
+                if (rge) { j.fromW = 1; j.base = x.w_off; j.ld = x.p; }
+                else { j.fromW = 0; j.base = x.v_off; j.ld = x.n; }
+                ja.push_back(j);
+                mx = std::max(mx, j.rows * j.cols);
+            }
+            for (const auto& c : S.coff) {        // B blocks (m, s2) [k][c]
+                const int bb = SB.at(im, c.first.first);
+                if (bb < 0) continue;
+                ScatJob j{};
+                j.dst = SB.blk[bb].off; j.rows = SB.blk[bb].rows; j.cols = SB.blk[bb].cols;
+                j.s_off = x.s_off; j.off0 = c.second; j.left = 0; j.lam_pow = R.lam_pow_right;
+                if (rge) { j.fromW = 0; j.base = x.v_off; j.ld = x.n; }
+                else { j.fromW = 1; j.base = x.w_off; j.ld = x.p; }
+                jb.push_back(j);
+                mx = std::max(mx, j.rows * j.cols);
+            }
         }
-    PD_REQUIRE(res.mid.n() > 0, DMRG_ERR_NUMERIC, "SVD kept no singular value (zero wavefunction?)");
-    res.trunc = wts[0] > 0 ? std::max(0.0, (wts[0] - wts[1]) / wts[0]) : 0.0;
-    // scatter
-    const SiteLayout SA = site_layout(bl, res.mid, qn1);
-    const SiteLayout SB = site_layout(res.mid, br, qn2);
-    std::vector<ScatJob> jobs;
-    int mx = 1;
-    for (int s = 0; s < nsec; ++s) {
-        if (!kept_of_sec[s]) continue;
-        const auto& S = *order_secs[s];
-        int im = res.mid.find(S.qm);
-        bool rge = S.r >= S.c;
-        for (const auto& r : S.roff) {        // A blocks (i, s1) [a][k]
-            int ab = SA.at(r.first.first, r.first.second);
-            if (ab < 0) continue;
-            ScatJob j{};
-            j.dst = SA.blk[ab].off; j.rows = SA.blk[ab].rows; j.cols = SA.blk[ab].cols;
-            j.s_off = ss[s].s_off; j.off0 = r.second; j.left = 1; j.lam_pow = lam_pow_left;
-            if (rge) { j.fromW = 1; j.base = ss[s].w_off; j.ld = ss[s].p; }
-            else { j.fromW = 0; j.base = ss[s].v_off; j.ld = ss[s].n; }
-            jobs.push_back(j);
-            mx = std::max(mx, j.rows * j.cols);
+        const double* wq = dwts.as<double>() + 2 * q;
+        auto scatter = [&](const std::vector<ScatJob>& jobs_, double* dst) {
+            if (jobs_.empty()) return;
+            keep_alive.emplace_back();
+            DBuf& dj = keep_alive.back();
+            upload(dj, jobs_, st);
+            dim3 g(gridn(mx, 256), (unsigned)jobs_.size());
+            if (fp32)
+                k_svd_scatter<float><<<g, 256, 0, st>>>(dj.as<ScatJob>(), dW.as<float>(), dV.as<float>(),
+                                                        dsig.as<double>(), dord.as<int>(), wq, dst);
+            else
+                k_svd_scatter<double><<<g, 256, 0, st>>>(dj.as<ScatJob>(), dW.as<double>(), dV.as<double>(),
+                                                         dsig.as<double>(), dord.as<int>(), wq, dst);
+            PD_LAUNCHED();
+        };
+        scatter(ja, R.A_out);
+        scatter(jb, R.B_out);
+        // lambda
+        std::vector<LamJob> lj;
+        long long o = 0;
+        for (int s = 0; s < F.nsec; ++s) {
+            if (!kept_of_sec[s]) continue;
+            lj.push_back({ss[F.sec0 + s].s_off, o, kept_of_sec[s], 0});
+            o += kept_of_sec[s];
         }
-        for (const auto& c : S.coff) {        // B blocks (m, s2) [k][c]
-            int bb = SB.at(im, c.first.first);
-            if (bb < 0) continue;
-            ScatJob j{};
-            j.dst = SB.blk[bb].off + 0; j.rows = SB.blk[bb].rows; j.cols = SB.blk[bb].cols;
-            j.s_off = ss[s].s_off; j.off0 = c.second; j.left = 0; j.lam_pow = lam_pow_right;
-            if (rge) { j.fromW = 0; j.base = ss[s].v_off; j.ld = ss[s].n; }
-            else { j.fromW = 1; j.base = ss[s].w_off; j.ld = ss[s].p; }
-            // B lives in a separate buffer: mark with a negative sentinel handled below
-            j.pad_ = 1;
-            jobs.push_back(j);
-            mx = std::max(mx, j.rows * j.cols);
+        keep_alive.emplace_back();
+        DBuf& dlj = keep_alive.back();
+        upload(dlj, lj, st);
+        double* lam_dev = R.lam_out_dev;
+        if (!lam_dev) {
+            keep_alive.emplace_back();
+            DBuf& dlam = keep_alive.back();
+            dlam.ensure(o * 8, st);
+            lam_dev = dlam.as<double>();
         }
-    }
-    std::vector<ScatJob> ja, jb;
-    for (auto& j : jobs) (j.pad_ ? jb : ja).push_back(j);
-    DBuf dja, djb;
-    upload(dja, ja, st);
-    upload(djb, jb, st);
-    auto scatter = [&](const std::vector<ScatJob>& jobs_, const DBuf& dj, double* out) {
-        if (jobs_.empty()) return;
-        dim3 g(gridn(mx, 256), (unsigned)jobs_.size());
-        if (fp32)
-            k_svd_scatter<float><<<g, 256, 0, st>>>(dj.as<ScatJob>(), dW.as<float>(), dV.as<float>(), dsig.as<double>(),
-                                                    dord.as<int>(), dwts.as<double>(), out);
-        else
-            k_svd_scatter<double><<<g, 256, 0, st>>>(dj.as<ScatJob>(), dW.as<double>(), dV.as<double>(),
-                                                     dsig.as<double>(), dord.as<int>(), dwts.as<double>(), out);
+        k_lam_out<<<std::max<int>(1, (int)lj.size()), 128, 0, st>>>(dlj.as<LamJob>(), (int)lj.size(),
+                                                                     dsig.as<double>(), dord.as<int>(), wq, lam_dev);
         PD_LAUNCHED();
-    };
-    scatter(ja, dja, A_out);
-    scatter(jb, djb, B_out);
-    // lambda
-    std::vector<LamJob> lj;
-    long long o = 0;
-    for (int s = 0; s < nsec; ++s) {
-        if (!kept_of_sec[s]) continue;
-        lj.push_back({ss[s].s_off, o, kept_of_sec[s], 0});
-        o += kept_of_sec[s];
+        res.lam.resize(o);
+        PD_CK(cudaMemcpyAsync(res.lam.data(), lam_dev, o * 8, cudaMemcpyDeviceToHost, st));
     }
-    DBuf dlj, dlam;
-    upload(dlj, lj, st);
-    double* lam_dev = lam_out_dev;
-    if (!lam_dev) {
-        dlam.ensure(o * 8, st);
-        lam_dev = dlam.as<double>();
-    }
-    k_lam_out<<<std::max<int>(1, (int)lj.size()), 128, 0, st>>>(dlj.as<LamJob>(), (int)lj.size(), dsig.as<double>(),
-                                                                 dord.as<int>(), dwts.as<double>(), lam_dev);
-    PD_LAUNCHED();
-    res.lam.resize(o);
-    PD_CK(cudaMemcpyAsync(res.lam.data(), lam_dev, o * 8, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
-    return res;
+    return out;
+}
+
+SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1, const std::vector<int>& qn2,
+                      const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
+                      int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st,
+                      bool fp32) {
+    SplitReq r;
+    r.bl = bl;
+    r.br = br;
+    r.qn1 = &qn1;
+    r.qn2 = &qn2;
+    r.psi = psi;
+    r.m_max = m_max;
+    r.rel_cutoff = rel_cutoff;
+    r.lam_pow_left = lam_pow_left;
+    r.lam_pow_right = lam_pow_right;
+    r.A_out = A_out;
+    r.B_out = B_out;
+    r.lam_out_dev = lam_out_dev;
+    return std::move(svd_split_batch({r}, accurate, fp32, st)[0]);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -354,6 +354,24 @@ SplitResult svd_split(const Sec& bl, const Sec& br, const std::vector<int>& qn1,
                       const double* psi, int m_max, double rel_cutoff, bool accurate, int lam_pow_left,
                       int lam_pow_right, double* A_out, double* B_out, double* lam_out_dev, cudaStream_t st,
                       bool fp32 = false);
+// One bond's split inside svd_split_batch (same meaning as svd_split's arguments).
+struct SplitReq {
+    Sec bl, br;
+    const std::vector<int>* qn1 = nullptr;
+    const std::vector<int>* qn2 = nullptr;
+    const double* psi = nullptr;
+    int m_max = 0;
+    double rel_cutoff = 1e-12;
+    int lam_pow_left = 0, lam_pow_right = 0;
+    double* A_out = nullptr;
+    double* B_out = nullptr;
+    double* lam_out_dev = nullptr;
+};
+// The splits of several bonds in one pass: the charge sectors of all bonds form one batch of the
+// Jacobi SVD (one cooperative launch), truncation (each bond's own keep-m rule), scatter and
+// lambda then run per bond.  All psi must be ready on st; the outputs are written on st.
+std::vector<SplitResult> svd_split_batch(const std::vector<SplitReq>& reqs, bool accurate, bool fp32,
+                                         cudaStream_t st);
 // FP64 re-orthonormalisation of the kept factor after a reduced-precision SVD: one Newton-Schulz
 // step per middle sector, X <- X (3I - X^T X)/2 for a left factor (blocks bl x br, kept index on
 // br), X <- (3I - X X^T)/2 X for a right factor (kept index on bl).

@@ -45,7 +45,7 @@ struct Rec {
 std::mutex g_mu;
 std::atomic<bool> g_on{false};
 std::vector<Rec> g_pending;
-long long g_svd_calls = 0, g_svd_sweeps = 0, g_svd_block = 0, g_svd_f64 = 0, g_svd_rows = 0;
+long long g_svd_calls = 0, g_svd_sweeps = 0, g_svd_block = 0, g_svd_f64 = 0, g_svd_rows = 0, g_svd_bonds = 0;
 double g_svd_ms = 0.0, g_svd_block_ms = 0.0, g_svd_f64_ms = 0.0, g_svd_block_flops = 0.0;
 long long g_rot_hist[48] = {0};
 double g_ms[4] = {0, 0, 0, 0}, g_fl[4] = {0, 0, 0, 0};
@@ -73,9 +73,11 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops) {
     delete[] ev;
 }
 
-void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist) {
+void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist,
+              int bonds) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_svd_calls += 1;
+    g_svd_bonds += bonds;
     g_svd_sweeps += sweeps;
     g_svd_ms += ms;
     if (kind == 1) g_svd_block += 1, g_svd_block_ms += ms, g_svd_block_flops += flops;
@@ -101,7 +103,7 @@ void dmrg_profile_reset(void) {
     }
     g_pending.clear();
     for (int i = 0; i < 4; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
-    g_svd_calls = g_svd_sweeps = g_svd_block = g_svd_f64 = g_svd_rows = 0;
+    g_svd_calls = g_svd_sweeps = g_svd_block = g_svd_f64 = g_svd_rows = g_svd_bonds = 0;
     g_svd_ms = g_svd_block_ms = g_svd_f64_ms = g_svd_block_flops = 0.0;
     for (auto& x : g_rot_hist) x = 0;
     g_launches.store(0);
@@ -138,6 +140,7 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->f32_gemm_ms = g_ms[PROF_F32];
     out->f32_gemm_flops = g_fl[PROF_F32];
     out->svd_calls = g_svd_calls;
+    out->svd_bonds = g_svd_bonds;
     out->svd_sweeps = g_svd_sweeps;
     out->svd_ms = g_svd_ms;
     out->svd_block_calls = g_svd_block;

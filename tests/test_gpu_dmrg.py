@@ -167,13 +167,15 @@ def test_state_export_round_trip():
     eng2.close()
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("R", [2, 4])
-def test_regions_cylinder_serial_schedule(R):
+def test_regions_cylinder_serial_schedule(R, schedule):
     """6x4 Heisenberg cylinder with a random longitudinal field (2-D snake MPO, D = 14; the field
     lifts the SU(2) and spin-flip degeneracies of the Schmidt values, so the cut has no
     symmetry-enforced near-ties), m = 128 in the set-up and the sweeps, the regions of each Fig. 4
-    phase driven one after another by the calling thread (serial_regions = 1, cooperative Jacobi
-    launches inside the regions): region centres, sweep energies and merge fidelities match the
+    phase driven by the calling thread -- one after another (serial_regions = 1, cooperative Jacobi
+    launches inside the regions) or in lockstep, bond step by bond step (serial_regions = 2):
+    region centres, sweep energies and merge fidelities match the
     FP64 oracle sweep by sweep, and so do the bond tables of every bond the truncation cuts at m
     (bonds kept whole end in singular values near the 1e-12 cutoff, whose vectors are not
     determined by the wavefunction)."""
@@ -185,12 +187,12 @@ def test_regions_cylinder_serial_schedule(R):
     ref.setup(m, warmup_sweeps=1)
     eng = engine_for(pd, mpo)
     load_mps(eng, mps, qn)
-    eng.setup_regions(R, 1, m, serial_regions=1)
+    eng.setup_regions(R, 1, m, serial_regions=schedule)
     for k in range(R):
         assert eng.center(k) == ref.regions[k].oc
     for sweep in range(2):
         r = ref.sweep(m)
-        g = eng.sweep(m, serial_regions=1)
+        g = eng.sweep(m, serial_regions=schedule)
         assert abs(g["energy"] - r["energy"]) <= TOL * abs(r["energy"]), sweep
         fids = [x["fidelity"] for x in r["merges"]]
         assert abs(g["max_fidelity"] - max(fids)) <= 1e-7 * max(1.0, max(fids)), (g["max_fidelity"], fids)
@@ -226,6 +228,44 @@ def test_regions_cylinder_serial_schedule_bf16():
         g = eng.sweep(m, **dav)
     assert abs(g["energy"] - r["energy"]) <= 2e-5 * abs(r["energy"]), (g["energy"], r["energy"])
     eng.close()
+
+
+def test_regions_lockstep_bf16_matches_serial():
+    """The bench's mixed-precision path with the regions in lockstep (serial_regions = 2: every
+    Fig. 4 phase's FP32 splits of all regions in one grouped block-Jacobi launch) against the same
+    engine with the regions one after another (serial_regions = 1) and the FP64 oracle's converged
+    serial energy: the two schedules differ only by the rounding of the FP32 splits, so their
+    sweep energies agree to 2e-6 and both reach the oracle's to 2e-5 (the mixed engine's own
+    accuracy on FP32 environments); the same bonds are split, in fewer split passes."""
+    mpo = wl.field_square_cylinder(6, 4, seed=3)
+    qn = list(mpo.site.qn)
+    mps = wl.random_mps(mpo.L, qn, 0, 16, seed=2)
+    ref = O.SerialDMRG(mpo, mps)
+    for m in (64, 128, 128, 128):
+        r = ref.sweep(m)
+    out = []
+    for schedule in (1, 2):
+        eng = engine_for(pd, mpo, precision="bf16")
+        load_mps(eng, mps, qn)
+        dav = dict(dav_tol=1e-9, dav_max_iter=12, refine_iters=6, serial_regions=schedule)
+        eng.setup_regions(4, 1, 96, **dav)
+        pd.profile_enable(True)
+        pd.profile_reset()
+        gs = [eng.sweep(m, **dav) for m in (96, 128, 128, 128)]
+        prof = pd.profile_read()
+        pd.profile_enable(False)
+        out.append((gs, [eng.bond(b) for b in range(mpo.L + 1)], prof))
+        eng.close()
+    (g1, b1, p1), (g2, b2, p2) = out
+    for x, y in zip(g1, g2):
+        assert abs(x["energy"] - y["energy"]) <= 2e-6 * abs(x["energy"]), (x["energy"], y["energy"])
+    for g in (g1[-1], g2[-1]):
+        assert abs(g["energy"] - r["energy"]) <= 2e-5 * abs(r["energy"]), (g["energy"], r["energy"])
+    assert all(sum(x.values()) <= 128 for x in b2)
+    # (an FP32 split refused by the FP64 re-orthonormalisation is redone alone in FP64)
+    assert p1["svd_bonds"] - p1["svd_fp64_fallbacks"] == p2["svd_bonds"] - p2["svd_fp64_fallbacks"]
+    assert p2["svd_calls"] < p2["svd_bonds"] / 2
+    assert p1["svd_calls"] == p1["svd_bonds"]
 
 
 def test_region_state_export():

@@ -220,6 +220,93 @@ def test_svd_split_fp32_block_jacobi(kind, m, mmax, plain):
     assert np.sqrt(diff) <= 2e-4 + 2 * np.sqrt(err)
 
 
+@pytest.mark.parametrize("mode", [0, 2, 6])
+def test_svd_split_batch_equals_single_splits(mode):
+    """dmrg_svd_split_batch over four bonds of different shapes and charge sets (chain, cylinder,
+    TFIM, a tiny chain bond; one grouped Jacobi launch over all their sectors) returns, bond by
+    bond, what dmrg_svd_split returns for that bond alone -- same block table, discarded weight,
+    lambda and factors -- and what the oracle returns: FP64 mode (0) to 1e-12; the FP32 block
+    Jacobi (2, and 6 without the QR) to the FP32 split's bounds (lambda 1e-4 lambda_max, the
+    reconstruction 2e-4 normwise), lambda to 1e-5 lambda_max of the single-bond FP32 run
+    (thresholds are per sector; the staging of a sector's columns, and so the rounding of its
+    rotations, follows the batch's largest sector)."""
+    cases = [("chain", 200, 120), ("cyl", 420, 300), ("tfim", 80, 50), ("chain", 12, 6)]
+    fp32 = (mode & 3) == 2
+    bonds, xs, single, batch, refs, mmaxs = [], [], [], [], [], []
+    for i, (kind, m, mmax) in enumerate(cases):
+        mpo, qn, bl, br, _, j, rng = _bond_case(kind, m, 11 + i)
+        psi = {}
+        for k in LY.psi_keys(bl, br, qn):
+            a, c = bl[k[0]], br[k[0] + qn[k[1]] + qn[k[2]]]
+            psi[k] = rng.standard_normal((a, c)) * np.exp(-0.02 * np.add.outer(np.arange(a), np.arange(c)))
+        nrm = np.sqrt(sum((v ** 2).sum() for v in psi.values()))
+        psi = {k: v / nrm for k, v in psi.items()}
+        bond = pd.Bond(qn, bl, br, mpo.W[j], mpo.flux[j], mpo.flux[j + 1])
+        x = _dev(LY.pack_psi(psi, bl, br, qn))
+        n = x.numel()
+        s_bufs = [torch.zeros(n + 16, dtype=torch.float64, device="cuda") for _ in range(3)]
+        b_bufs = [torch.zeros(n + 16, dtype=torch.float64, device="cuda") for _ in range(3)]
+        mid, tr = pd.svd_split(bond, x.data_ptr(), mmax, mode, s_bufs[0].data_ptr(), s_bufs[1].data_ptr(),
+                               s_bufs[2].data_ptr())
+        single.append((mid, tr, s_bufs))
+        batch.append(b_bufs)
+        bonds.append(bond)
+        xs.append(x)
+        mmaxs.append(mmax)
+        refs.append((qn, bl, br, O.split_two_site(psi, bl, br, qn, mmax),
+                     O.split_two_site(psi, bl, br, qn, 10 ** 9)[1]))
+    res = pd.svd_split_batch(bonds, [x.data_ptr() for x in xs], mmaxs, mode, [b[0].data_ptr() for b in batch],
+                             [b[1].data_ptr() for b in batch], [b[2].data_ptr() for b in batch])
+    torch.cuda.synchronize()
+    assert len(res) == len(cases)
+    for (mid_b, tr_b), (mid_s, tr_s, s_bufs), b_bufs, (qn, bl, br, ref, full), mmax in zip(
+            res, single, batch, refs, mmaxs):
+        A, lam, B, counts, err = ref
+        spec = np.sort(np.concatenate(list(full.values())))[::-1]
+        resolvable = len(spec) <= mmax or (spec[mmax - 1] - spec[mmax] > 1e-4 * spec[0]
+                                           and spec[mmax - 1] > 1e-4 * spec[0])
+        if not fp32 or resolvable:
+            assert mid_b == counts
+        assert mid_b == mid_s
+        kept = int(sum(mid_b.values()))
+        lam_b = b_bufs[1].cpu().numpy()[:kept]
+        lam_s = s_bufs[1].cpu().numpy()[:kept]
+        lam_ref = np.concatenate([lam[q] for q in sorted(lam)]) if not fp32 else None
+        if fp32:
+            assert np.abs(lam_b - lam_s).max() <= 1e-5 * spec[0]
+            got = np.sort(lam_b)[::-1]
+            assert np.abs(got - spec[:kept] / np.sqrt((spec[:kept] ** 2).sum())).max() <= 1e-4 * spec[0]
+            assert abs(tr_b - tr_s) <= 1e-5
+        else:
+            assert np.abs(lam_b - lam_ref).max() <= 1e-12
+            assert np.abs(lam_b - lam_s).max() <= 1e-13
+            assert abs(tr_b - err) <= 1e-12 + 1e-9 * err
+        Ab = LY.unpack_site(b_bufs[0].cpu().numpy(), bl, mid_b, qn)
+        Bb = LY.unpack_site(b_bufs[2].cpu().numpy(), mid_b, br, qn)
+        As = LY.unpack_site(s_bufs[0].cpu().numpy(), bl, mid_s, qn)
+        Bs = LY.unpack_site(s_bufs[2].cpu().numpy(), mid_s, br, qn)
+        lg, off = {}, 0
+        for q in sorted(mid_b):
+            lg[q] = lam_b[off: off + mid_b[q]]
+            off += mid_b[q]
+        ls, off = {}, 0
+        for q in sorted(mid_s):
+            ls[q] = lam_s[off: off + mid_s[q]]
+            off += mid_s[q]
+        rec_b = O.two_site({k: v * lg[k[0] + qn[k[1]]][None, :] for k, v in Ab.items()}, Bb, qn)
+        rec_s = O.two_site({k: v * ls[k[0] + qn[k[1]]][None, :] for k, v in As.items()}, Bs, qn)
+        rec_o = O.two_site({k: v * lam[k[0] + qn[k[1]]][None, :] for k, v in A.items()}, B, qn)
+        if fp32:   # normwise
+            d_bs = np.sqrt(sum(((rec_b.get(k, 0) - rec_s.get(k, 0)) ** 2).sum() for k in rec_o))
+            d_bo = np.sqrt(sum(((rec_b.get(k, 0) - rec_o[k]) ** 2).sum() for k in rec_o))
+            assert d_bs <= 2e-4 + 2 * np.sqrt(err)
+            assert d_bo <= 2e-4 + 2 * np.sqrt(err)
+        else:      # element by element
+            for k in rec_o:
+                assert np.abs(rec_b[k] - rec_s[k]).max() <= 1e-12, k
+                assert np.abs(rec_b[k] - rec_o[k]).max() <= 1e-11, k
+
+
 # ------------------------------------------------------------------------------------------
 # Tensor-core (tcgen05) paths against the FP64 oracle, element by element and normwise.  Every
 # product term L W1 W2 R x of an output element passes through at most four operand roundings
