@@ -152,7 +152,8 @@ typedef struct {
     double seconds;         /* host wall time of the call (synchronised)                      */
     double matvec_seconds;  /* summed device time of the matvecs (CUDA events)                */
     double matvec_flops;    /* algorithmic flops of those matvecs (nonzero blocks only)       */
-    double min_fidelity;    /* smallest merge fidelity 1-|<Psi'|Psi>| of the sweep (-1: none)  */
+    double min_fidelity;    /* smallest merge fidelity 1-|<Psi'|Psi>| of the sweep (-1: none;
+                               an exact prediction can round a few ulps below 0)              */
     double max_fidelity;    /* largest merge fidelity of the sweep (-1: none)                 */
     int n_refine_matvec;    /* FP32-accurate refinement matvecs (mixed modes)                 */
     double refine_seconds;  /* their summed device time                                       */

@@ -21,6 +21,13 @@
 // with noise = c * eps_f32 * sigma_max: the second term is the absolute rounding level of FP32
 // columns of a matrix whose largest singular value is sigma_max.  Pairs below it are left as
 // they are; their effect on the kept weight is below eps_f32 * sigma_max^2.
+//
+// Unchanged pairs are skipped: every block records the time (sweep * rounds + round + 1) it was
+// last rotated, every block pair the time it was last found converged; a pair found converged
+// after both of its blocks' last rotations has the same Gram matrix as then (and the noise level
+// only grows), so it is converged still and is not staged again.  In a round a block belongs to
+// one pair only, so each stamp has one writer per round; they are read after the round's grid
+// barrier (or kernel boundary), from L2.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -53,6 +60,7 @@ struct alignas(16) BjShared {
     unsigned char lo[BJ_K - 1][BJ_NP], hi[BJ_K - 1][BJ_NP];   // inner round-robin pairs
     float noise;
     int flag[2];                       // any rotation in the inner round (by round parity)
+    int qitem, qok;                    // work queue: item taken by this CTA, its state
 };
 static_assert(sizeof(BjShared) % 16 == 0, "staging area must stay 16-byte aligned");
 
@@ -328,19 +336,24 @@ __device__ __forceinline__ void bj_rotate_streamed(float* __restrict__ X, float*
 // for the Gram matrix, once for the rotation).
 __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict__ XV, int cap, const SvdSec& s,
                         const BjSec& b, int si, int pi, int round, float* __restrict__ W, float* __restrict__ V,
-                        float tol, float noise_c, float* __restrict__ gmax, int inner_sweeps) {
-    int cI, kI, cJ, kJ;
+                        float tol, float noise_c, float* __restrict__ gmax, int inner_sweeps,
+                        int* __restrict__ bmod, int* __restrict__ pchk, int now) {
+    int cI, kI, cJ, kJ, I = 0, J = 0;
     if (b.nb == 1) {
         if (round != 0) return 0.0;
         cI = 0; kI = s.n; cJ = 0; kJ = 0;
     } else {
         if (round >= b.nbp - 1) return 0.0;
-        int I = rr_pos(pi, round, b.nbp), J = rr_pos(b.nbp - 1 - pi, round, b.nbp);
+        I = rr_pos(pi, round, b.nbp);
+        J = rr_pos(b.nbp - 1 - pi, round, b.nbp);
         if (I > J) { const int t = I; I = J; J = t; }
         if (J >= b.nb) return 0.0;
         cI = I * BJ_B; kI = min(BJ_B, s.n - cI);
         cJ = J * BJ_B; kJ = min(BJ_B, s.n - cJ);
     }
+    // skip a pair found converged after both blocks' last rotations (same values in every thread)
+    int* const chk = pchk + b.pst0 + I * b.nb + J;
+    if (__ldcg(chk) > max(__ldcg(bmod + b.blk0 + I), __ldcg(bmod + b.blk0 + J))) return 0.0;
     const int k = kI + kJ;
     const int tid = threadIdx.x;
     const double gram_flops = 2.0 * s.p * k * k, rot_flops = 2.0 * ((double)s.p + s.n) * k * k;
@@ -398,6 +411,7 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
     if (!__syncthreads_or(need)) {
         cp_async_wait<0>();
         __syncthreads();
+        if (tid == 0) *chk = now;
         return gram_flops;
     }
     bj_inner(S, inner_sweeps, tol, noise);
@@ -435,6 +449,7 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
             __syncthreads();
             bj_unstage(XV, V + s.v_off, s.n, 0, s.n, S.gcol, k);
             __syncthreads();
+            if (tid == 0) bmod[b.blk0 + I] = bmod[b.blk0 + J] = now;
             return -(gram_flops + rot_flops);
         }
         __syncthreads();
@@ -443,6 +458,7 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
     }
     bj_rotate_global(V + s.v_off, s.n, s.n, Qp, S.gcol, k);
     __syncthreads();
+    if (tid == 0) bmod[b.blk0 + I] = bmod[b.blk0 + J] = now;
     return -(gram_flops + rot_flops);
 }
 
@@ -452,8 +468,9 @@ __device__ double bj_task(BjShared& S, float* __restrict__ XW, float* __restrict
 // of the one before).
 __global__ void __launch_bounds__(BJ_THREADS, 1)
     k_bjacobi_round(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
-                    int ntasks, int round, int sweep, int inner_sweeps, int max_p, int split, float* __restrict__ W,
-                    float* __restrict__ V, float noise_c, float* __restrict__ gmax, int* __restrict__ rot,
+                    int ntasks, int round, int sweep, int nrounds, int inner_sweeps, int max_p, int split,
+                    float* __restrict__ W, float* __restrict__ V, float noise_c, float* __restrict__ gmax,
+                    int* __restrict__ bmod, int* __restrict__ pchk, int* __restrict__ rot,
                     unsigned long long* __restrict__ flops) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     if (sweep > 0 && *((volatile int*)&rot[sweep - 1]) == 0) return;
@@ -473,56 +490,118 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
         const SvdSec s = secs[si];
         const BjSec b = bsecs[si];
         const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, b.tol, noise_c, gmax,
-                                 inner_sweeps);
+                                 inner_sweeps, bmod, pchk, sweep * nrounds + round + 1);
         fl += fabs(r);
         if (r < 0.0 && threadIdx.x == 0) atomicAdd(&rot[sweep], 1);
     }
     if (threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, (unsigned long long)fl);
 }
 
-// All sweeps in one cooperative launch, for a caller that has the GPU to itself: a bounded grid
-// barrier ends each round (cheaper than a kernel boundary).  rot[sweep] counts rotated pairs
-// (zeroed by the host); *sweeps = sweeps run; bar: 3 zeroed words for the barrier.
+// All sweeps in one cooperative launch, for a caller that has the GPU to itself, without grid-wide
+// barriers.  Work items (sweep, round, sector, pair) are taken in order from one counter: per sweep
+// the rounds in order, in each round every sector's pairs (taller sectors first).  An item waits
+// only for the previous round of its own sector (the sector's count of finished items), since
+// sectors are independent: the small sectors run ahead into later sweeps while the tall sectors'
+// long round sequences are in flight, instead of every round of every sector waiting for the
+// slowest pair of the whole batch.  Items depend on earlier items only and every CTA is resident,
+// so the queue always drains.  A sector whose sweep rotated nothing has converged: its later items
+// are counted without work, and the launch ends once every sector has converged (or after
+// max_sweeps; nact = sectors with columns).  A dependency wait is bounded (ERRBIT_TIMEOUT and the
+// abort flag after 2 s).
+// qstate (zeroed): [0] next item, [1] converged sectors, [2] abort flag, then finished items per
+// sector (nsec), converged flags (nsec), pairs rotated per sector and sweep (nsec x max_sweeps).
+// rot[sweep]: pairs rotated in that sweep over all sectors; *sweeps: sweeps run by the slowest
+// sector.
 __global__ void __launch_bounds__(BJ_THREADS, 1)
-    k_bjacobi_coop(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int* __restrict__ task_sec,
-                   int ntasks, int nrounds, int max_sweeps, int inner_sweeps, int max_p, int split,
-                   float* __restrict__ W, float* __restrict__ V, float noise_c, float* __restrict__ gmax,
-                   int* __restrict__ rot, int* __restrict__ sweeps, unsigned* __restrict__ bar,
-                   unsigned* __restrict__ err, unsigned long long* __restrict__ flops) {
+    k_bjacobi_queue(const SvdSec* __restrict__ secs, const BjSec* __restrict__ bsecs, const int2* __restrict__ items,
+                    int per_sweep, int nsec, int nact, int nrounds, int max_sweeps, int inner_sweeps, int max_p,
+                    int split,
+                    float* __restrict__ W, float* __restrict__ V, float noise_c, float* __restrict__ gmax,
+                    int* __restrict__ bmod, int* __restrict__ pchk, int* __restrict__ qstate, int* __restrict__ rot,
+                    int* __restrict__ sweeps, unsigned* __restrict__ err, unsigned long long* __restrict__ flops) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     BjShared& S = *reinterpret_cast<BjShared*>(bj_smem);
     float* XW = reinterpret_cast<float*>(bj_smem + sizeof(BjShared));
     float* XV = split ? XW + (size_t)max_p * BJ_LD : XW;
-    for (int e = threadIdx.x; e < (BJ_K - 1) * BJ_NP; e += blockDim.x) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < (BJ_K - 1) * BJ_NP; e += blockDim.x) {
         const int rnd = e / BJ_NP, i = e % BJ_NP;
         const int a = rr_pos(i, rnd, BJ_K), b = rr_pos(BJ_K - 1 - i, rnd, BJ_K);
         S.lo[rnd][i] = (unsigned char)min(a, b);
         S.hi[rnd][i] = (unsigned char)max(a, b);
     }
-    __syncthreads();
-    int done = 0;
-    bool alive = true;
+    int* const qnext = qstate;
+    int* const nconv = qstate + 1;
+    int* const abort_flag = qstate + 2;
+    int* const done = qstate + 3;
+    int* const conv = done + nsec;
+    int* const srot = conv + nsec;
+    const long long total = (long long)per_sweep * max_sweeps;
     double fl = 0.0;
-    while (done < max_sweeps && alive) {
-        const int sweep = done;
-        for (int round = 0; round < nrounds && alive; ++round) {
-            for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-                const int si = task_sec[t];
-                const SvdSec s = secs[si];
-                const BjSec b = bsecs[si];
-                const double r = bj_task(S, XW, XV, max_p, s, b, si, t - b.task0, round, W, V, b.tol, noise_c, gmax,
-                                         inner_sweeps);
-                fl += fabs(r);
-                if (r < 0.0 && threadIdx.x == 0) atomicAdd(&rot[sweep], 1);
+    for (;;) {
+        if (tid == 0) S.qitem = atomicAdd(qnext, 1);
+        __syncthreads();
+        const long long i = S.qitem;
+        if (i >= total) break;                       // uniform: read before anyone writes it again
+        const int sweep = (int)(i / per_sweep);
+        const int2 it = items[i - (long long)sweep * per_sweep];
+        const int si = it.x, round = it.y >> 16, pi = it.y & 0xffff;
+        const BjSec b = bsecs[si];
+        const int nr = b.nb == 1 ? 1 : b.nbp - 1;
+        if (tid == 0) {
+            int state = 1;                           // 1: work, 0: count only, -1: count and leave
+            if (*((volatile int*)abort_flag) != 0 || *((volatile int*)nconv) >= nact) state = -1;
+            else if (*((volatile int*)&conv[si]) != 0) state = 0;
+            if (state == 1) {
+                const int need = (sweep * nr + round) * b.ntask;
+                uint64_t t0;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+                while (*((volatile int*)&done[si]) < need) {
+                    if (*((volatile int*)abort_flag) != 0) { state = -1; break; }
+                    uint64_t t;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (t - t0 > 2000000000ull) {
+                        atomicOr(err, ERRBIT_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        state = -1;
+                        break;
+                    }
+                }
+                // the sector's earlier rounds (columns, stamps) happen before this item's loads
+                __threadfence();
             }
-            alive = grid_barrier(bar, gridDim.x, err);
+            S.qok = state;
         }
-        if (!alive) break;
-        ++done;
-        if (*((volatile int*)&rot[sweep]) == 0) break;
+        __syncthreads();
+        const int state = S.qok;
+        if (state == 1) {
+            const SvdSec s = secs[si];
+            const double r = bj_task(S, XW, XV, max_p, s, b, si, pi, round, W, V, b.tol, noise_c, gmax,
+                                     inner_sweeps, bmod, pchk, sweep * nrounds + round + 1);
+            fl += fabs(r);
+            if (r < 0.0 && tid == 0) {
+                atomicAdd(&srot[si * max_sweeps + sweep], 1);
+                atomicAdd(&rot[sweep], 1);
+            }
+        }
+        __syncthreads();                             // every thread's writes precede the count
+        if (tid == 0) {
+            __threadfence();
+            const int old = atomicAdd(&done[si], 1);
+            if (old + 1 == (sweep + 1) * nr * b.ntask) {   // the last item of this sector's sweep
+                __threadfence();
+                if (*((volatile int*)&conv[si]) == 0) {
+                    atomicMax(sweeps, sweep + 1);
+                    if (*((volatile int*)&srot[si * max_sweeps + sweep]) == 0) {
+                        atomicExch(&conv[si], 1);
+                        atomicAdd(nconv, 1);
+                    }
+                }
+            }
+        }
+        if (state < 0) break;
     }
-    if (threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, (unsigned long long)fl);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = done;
+    if (tid == 0 && fl > 0.0) atomicAdd(flops, (unsigned long long)fl);
 }
 
 }  // namespace
@@ -531,7 +610,8 @@ int bjacobi_max_rows() { return (int)((BJ_SMEM_MAX - sizeof(BjShared)) / (BJ_LD 
 
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
                     int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float noise_c,
-                    float* gmax, int* rot, int* sweeps, unsigned* bar, unsigned* err, unsigned long long* flops,
+                    float* gmax, int* bmod, int* pchk, int* rot, int* sweeps, unsigned* bar, unsigned* err,
+                    unsigned long long* flops, const int2* items, int per_sweep, int nsec, int nact, int* qstate,
                     cudaStream_t st) {
     if (ntasks <= 0 || nrounds <= 0) {
         PD_CK(cudaMemsetAsync(sweeps, 0, sizeof(int), st));
@@ -552,20 +632,21 @@ void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec,
     PD_CK(cudaGetDevice(&dev));
     PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (g_sm_cap == 0) {
-        // the GPU is this caller's: all sweeps in one cooperative launch
+        // the GPU is this caller's: all sweeps in one cooperative launch (the dependency queue)
         static const cudaError_t attr_c =
-            cudaFuncSetAttribute(k_bjacobi_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, BJ_SMEM_MAX);
+            cudaFuncSetAttribute(k_bjacobi_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, BJ_SMEM_MAX);
         PD_CK(attr_c);
         int per_sm = 0;
-        PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi_coop, BJ_THREADS, smem));
+        PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi_queue, BJ_THREADS, smem));
         PD_REQUIRE(per_sm > 0, DMRG_ERR_CAPACITY, "block Jacobi: kernel does not fit on an SM");
-        const int cblocks = std::max(1, std::min(ntasks, per_sm * sms));
-        PD_CK(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
-        void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&task_sec, (void*)&ntasks, (void*)&nrounds,
+        const int cblocks = std::max(1, std::min(per_sweep, per_sm * sms));
+        PD_CK(cudaMemsetAsync(sweeps, 0, sizeof(int), st));
+        void* args[] = {(void*)&secs, (void*)&bsecs, (void*)&items, (void*)&per_sweep, (void*)&nsec, (void*)&nact,
+                        (void*)&nrounds,
                         (void*)&max_sweeps, (void*)&inner_sweeps, (void*)&max_rows, (void*)&split, (void*)&W,
-                        (void*)&V, (void*)&noise_c, (void*)&gmax, (void*)&rot, (void*)&sweeps,
-                        (void*)&bar, (void*)&err, (void*)&flops};
-        PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi_coop, cblocks, BJ_THREADS, args, smem, st));
+                        (void*)&V, (void*)&noise_c, (void*)&gmax, (void*)&bmod, (void*)&pchk, (void*)&qstate,
+                        (void*)&rot, (void*)&sweeps, (void*)&err, (void*)&flops};
+        PD_CK(cudaLaunchCooperativeKernel((void*)k_bjacobi_queue, cblocks, BJ_THREADS, args, smem, st));
         PD_LAUNCHED();
         return;
     }
@@ -581,8 +662,8 @@ void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec,
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
             for (int round = 0; round < nrounds; ++round) {
                 k_bjacobi_round<<<blocks, BJ_THREADS, smem, st>>>(secs, bsecs, task_sec, ntasks, round, sweep,
-                                                                   inner_sweeps, max_rows, split, W, V, noise_c,
-                                                                   gmax, rot, flops);
+                                                                   nrounds, inner_sweeps, max_rows, split, W, V,
+                                                                   noise_c, gmax, bmod, pchk, rot, flops);
                 PD_LAUNCHED();
             }
             PD_CK(cudaMemcpyAsync(hrot + sweep, rot + sweep, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -23,7 +23,10 @@ namespace {
 struct StepStats {
     double energy = 0.0, trunc = 0.0, mv_ms = 0.0, mv_flops = 0.0, acc_ms = 0.0;
     int m = 0, matvecs = 0, nonconv = 0, steps = 0, acc_matvecs = 0;
+    // merge fidelities 1 - |<Psi'|Psi>| (rounding can take an exact prediction a few ulps below 0,
+    // so "none yet" is the count, not a sentinel value)
     double fid_min = -1.0, fid_max = -1.0;
+    int nfid = 0;
     void merge(const StepStats& o) {
         trunc = std::max(trunc, o.trunc);
         m = std::max(m, o.m);
@@ -34,8 +37,11 @@ struct StepStats {
         mv_flops += o.mv_flops;
         acc_ms += o.acc_ms;
         acc_matvecs += o.acc_matvecs;
-        if (o.fid_min >= 0) fid_min = fid_min < 0 ? o.fid_min : std::min(fid_min, o.fid_min);
-        if (o.fid_max >= 0) fid_max = std::max(fid_max, o.fid_max);
+        if (o.nfid > 0) {
+            fid_min = nfid ? std::min(fid_min, o.fid_min) : o.fid_min;
+            fid_max = nfid ? std::max(fid_max, o.fid_max) : o.fid_max;
+            nfid += o.nfid;
+        }
     }
 };
 
@@ -604,8 +610,9 @@ void do_merge(dmrg_ctx* c, int k, const dmrg_sweep_params* p, double* fid_out, d
     double fid = 1.0 - std::fabs(ov);
     s.energy = r.theta;
     s.steps++;
-    s.fid_min = s.fid_min < 0 ? fid : std::min(s.fid_min, fid);
-    s.fid_max = std::max(s.fid_max, fid);
+    s.fid_min = s.nfid ? std::min(s.fid_min, fid) : fid;
+    s.fid_max = s.nfid ? std::max(s.fid_max, fid) : fid;
+    s.nfid++;
     long long na, nb, nl;
     svd_split_bounds(bl, br, c->qn, c->qn, &na, &nb, &nl);
     DBuf A, B;

@@ -210,15 +210,19 @@ void launch_jacobi(const SvdSec* secs, int nsec, const int* pair_sec, int npairs
 // nb = ceil(n / 16) blocks, nbp = nb rounded up to even, task0 = first task of the sector in a
 // round, ntask = tasks per round (nbp / 2; 1 when nb = 1).  task_sec[t] = sector of task t.
 // tol: the sector's relative rotation threshold (FP32 dot products of p-long columns carry about
-// eps * sqrt(p) relative noise, so it sits above that).
+// eps * sqrt(p) relative noise, so it sits above that).  blk0 / pst0: the sector's first entry in
+// the block and pair stamp arrays (nb and nb * nb entries).
 struct BjSec {
     int nb, nbp, task0, ntask;
     float tol;
+    int blk0, pst0;
 };
 int bjacobi_max_rows();
 void launch_bjacobi(const SvdSec* secs, const BjSec* bsecs, const int* task_sec, int ntasks, int nrounds, int max_rows,
                     int max_n, int max_sweeps, int inner_sweeps, float* W, float* V, float noise_c, float* gmax,
-                    int* rot, int* sweeps, unsigned* bar, unsigned* err, unsigned long long* flops, cudaStream_t st);
+                    int* bmod, int* pchk, int* rot, int* sweeps, unsigned* bar, unsigned* err,
+                    unsigned long long* flops, const int2* items, int per_sweep, int nsec, int nact, int* qstate,
+                    cudaStream_t st);
 template <class T>
 void launch_svd_finish(const SvdSec* secs, int nsec, const T* W, double* sig, int* order, cudaStream_t st);
 

@@ -1173,7 +1173,7 @@ void block_jacobi32(const std::vector<SvdSec>& ss, const SvdSec* dsecs, float* W
     const int nsec = (int)ss.size();
     std::vector<BjSec> bs(nsec);
     std::vector<int> task_sec;
-    int nrounds = 0;
+    int nrounds = 0, nblk = 0, npst = 0;
     for (int s = 0; s < nsec; ++s) {
         BjSec b{};
         b.nb = (ss[s].n + 15) / 16;
@@ -1182,18 +1182,48 @@ void block_jacobi32(const std::vector<SvdSec>& ss, const SvdSec* dsecs, float* W
         b.ntask = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp / 2);
         // each sector's own threshold, so a split's result does not depend on its batch
         b.tol = std::max(3e-5f, 16.0f * FLT_EPSILON * std::sqrt((float)std::max(1, ss[s].p)));
+        b.blk0 = nblk;
+        b.pst0 = npst;
+        nblk += b.nb;
+        npst += b.nb * b.nb;
         for (int t = 0; t < b.ntask; ++t) task_sec.push_back(s);
         if (b.nb > 0) nrounds = std::max(nrounds, b.nb == 1 ? 1 : b.nbp - 1);
         bs[s] = b;
     }
-    DBuf dbs, dts, dgmax;
+    // the dependency queue's items for one sweep: round by round, in each round the pairs of every
+    // sector that has the round, taller sectors first (their pairs are the longest)
+    std::vector<int> by_rows(nsec);
+    for (int s = 0; s < nsec; ++s) by_rows[s] = s;
+    std::stable_sort(by_rows.begin(), by_rows.end(), [&](int a, int b) { return ss[a].p > ss[b].p; });
+    std::vector<int2> items;
+    int nact = 0;
+    for (const BjSec& b : bs) nact += b.nb > 0;
+    for (int r = 0; r < nrounds; ++r)
+        for (int s : by_rows) {
+            const BjSec& b = bs[s];
+            const int nr = b.nb == 0 ? 0 : (b.nb == 1 ? 1 : b.nbp - 1);
+            if (r < nr)
+                for (int t = 0; t < b.ntask; ++t) items.push_back(make_int2(s, (r << 16) | t));
+        }
+    const int bj_sweeps = std::min(40, max_sweeps);   // sweep cap of the block Jacobi
+    PD_REQUIRE(nrounds < 32768 && (long long)items.size() * bj_sweeps < (1ll << 31), DMRG_ERR_CAPACITY,
+               "block Jacobi: too many work items");
+    DBuf dbs, dts, dgmax, dstamp, ditems, dq;
     upload(dbs, bs, st);
     upload(dts, task_sec, st);
+    upload(ditems, items, st);
+    const size_t nq = 3 + (size_t)nsec * (2 + bj_sweeps);
+    dq.ensure(nq * 4, st);
+    PD_CK(cudaMemsetAsync(dq.p, 0, nq * 4, st));
     dgmax.ensure(std::max(1, nsec) * 4, st);
     PD_CK(cudaMemsetAsync(dgmax.p, 0, std::max(1, nsec) * 4, st));
+    // block / pair stamps (zero: never rotated / never found converged)
+    dstamp.ensure((size_t)std::max(1, nblk + npst) * 4, st);
+    PD_CK(cudaMemsetAsync(dstamp.p, 0, (size_t)std::max(1, nblk + npst) * 4, st));
     PD_CK(cudaMemsetAsync(flops, 0, 8, st));
-    launch_bjacobi(dsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, max_n, 40, 2, W, V,
-                   8.0f * FLT_EPSILON, dgmax.as<float>(), rot, rot + max_sweeps, bar, err, flops, st);
+    launch_bjacobi(dsecs, dbs.as<BjSec>(), dts.as<int>(), (int)task_sec.size(), nrounds, max_rows, max_n, bj_sweeps, 2,
+                   W, V, 8.0f * FLT_EPSILON, dgmax.as<float>(), dstamp.as<int>(), dstamp.as<int>() + nblk, rot,
+                   rot + max_sweeps, bar, err, flops, ditems.as<int2>(), (int)items.size(), nsec, nact, dq.as<int>(), st);
 }
 
 // Preconditioning of an FP64 one-sided Jacobi SVD of the batch ss (W FP64, p x n at w_off): the FP32
