@@ -329,6 +329,10 @@ typedef struct {
                                     timing every width (process-wide, not reset)               */
     long long tune_changed;      /* of those, classes where the timing overruled the cost model  */
     long long svd_bonds;         /* bonds split by those passes                                   */
+    double svd_block_alg_flops;  /* FP32 splits: textbook SVD flops of their sector matrices, the
+                                    R-SVD with U and V, 4 p n^2 + 22 n^3 per p x n sector         */
+    double svd_block_alg_bytes;  /* FP32 splits: the sector matrices read once, U and V written
+                                    once (FP32), 4 (2 p n + n^2) per sector                      */
 } dmrg_profile;
 
 void dmrg_profile_enable(int on);

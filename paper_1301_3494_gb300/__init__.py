@@ -44,7 +44,8 @@ class Profile(C.Structure):
                 ("svd_block_ms", C.c_double), ("svd_fp64_ms", C.c_double), ("svd_max_rows", C.c_longlong),
                 ("svd_fp64_fallbacks", C.c_longlong), ("svd_block_flops", C.c_double),
                 ("svd_rot_hist", C.c_longlong * 48), ("emu_fallbacks", C.c_longlong), ("tune_classes", C.c_longlong),
-                ("tune_changed", C.c_longlong), ("svd_bonds", C.c_longlong)]
+                ("tune_changed", C.c_longlong), ("svd_bonds", C.c_longlong), ("svd_block_alg_flops", C.c_double),
+                ("svd_block_alg_bytes", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

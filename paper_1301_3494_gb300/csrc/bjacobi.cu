@@ -216,7 +216,8 @@ __device__ __forceinline__ void bj_rot(float gpp, float gqq, float gpq, float& c
 }
 
 // Two-sided cyclic Jacobi on the Gram matrix S.G (in place) with the rotation accumulated in
-// S.Q[0]; at most `sweeps` sweeps, fewer when a sweep rotates nothing.  Each inner round: the
+// S.Q[0]; at most `sweeps` sweeps, fewer when a sweep rotates nothing or no pair needs a rotation
+// before a later sweep.  Each inner round: the
 // first half-warp decides the 16 rotations; then every thread rotates one 2 x 2 block of G (rows
 // of pair t / 16, columns of pair t % 16; the blocks partition G, so in place) and two column
 // pairs of one row of Q.
@@ -227,6 +228,16 @@ __device__ __forceinline__ void bj_inner(BjShared& S, int sweeps, float tol, flo
     const int qu = tid >> 3, qj = 2 * (tid & 7);      // Q row, first column pair
     float* Qr = S.Q[0] + qu * BJ_QLD;
     for (int isw = 0; isw < sweeps; ++isw) {
+        if (isw > 0) {
+            // a later sweep only if some pair still needs a rotation (one block-wide test instead
+            // of 31 rounds of decisions; the outer test always holds before the first sweep)
+            int need = 0;
+            for (int e = tid; e < BJ_K * BJ_K; e += BJ_THREADS) {
+                const int u = e >> 5, v = e & 31;
+                if (u < v) need |= bj_need(S.G[u * BJ_LD + v], S.G[u * BJ_LD + u], S.G[v * BJ_LD + v], tol, noise);
+            }
+            if (!__syncthreads_or(need)) break;
+        }
         int any_sweep = 0;
         for (int rnd = 0; rnd < BJ_K - 1; ++rnd) {
             if (tid < 32) {

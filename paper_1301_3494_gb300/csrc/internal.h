@@ -54,7 +54,7 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops);
 // scalar Jacobi, 1: FP32 block Jacobi, 2: FP64; max_rows: the call's largest sector row count;
 // flops: the FP32 Gram and rotation flops of a block-Jacobi call; rot_hist: its rotations per sweep.
 void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist,
-              int bonds = 1);
+              int bonds = 1, double alg_flops = 0.0, double alg_bytes = 0.0);
 // An FP32 split redone in FP64 (counted always, not only while profiling).
 void prof_fallback();
 // An emulated FP64 GEMM batch sent to the FP64 units by its scale guard (counted always).

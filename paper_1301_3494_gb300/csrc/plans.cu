@@ -1601,7 +1601,14 @@ std::vector<SplitResult> svd_split_batch(const std::vector<SplitReq>& reqs, bool
         PD_CK(cudaStreamSynchronize(st));
         float ms = 0.f;
         PD_CK(cudaEventElapsedTime(&ms, sv0, sv1));
-        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl, fp32 ? hist.data() : nullptr, max_sweeps, nreq);
+        double alg_fl = 0.0, alg_b = 0.0;
+        for (const SvdSec& x : ss) {
+            const double p = x.p, n = x.n;
+            alg_fl += 4.0 * p * n * n + 22.0 * n * n * n;
+            alg_b += 4.0 * (2.0 * p * n + n * n);
+        }
+        prof_svd(sweeps, ms, fp32 ? 1 : 2, maxp, (double)fl, fp32 ? hist.data() : nullptr, max_sweeps, nreq, alg_fl,
+                 alg_b);
         cudaEventDestroy(sv0);
         cudaEventDestroy(sv1);
     }

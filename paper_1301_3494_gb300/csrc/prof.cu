@@ -47,6 +47,7 @@ std::atomic<bool> g_on{false};
 std::vector<Rec> g_pending;
 long long g_svd_calls = 0, g_svd_sweeps = 0, g_svd_block = 0, g_svd_f64 = 0, g_svd_rows = 0, g_svd_bonds = 0;
 double g_svd_ms = 0.0, g_svd_block_ms = 0.0, g_svd_f64_ms = 0.0, g_svd_block_flops = 0.0;
+double g_svd_block_alg_flops = 0.0, g_svd_block_alg_bytes = 0.0;
 long long g_rot_hist[48] = {0};
 double g_ms[4] = {0, 0, 0, 0}, g_fl[4] = {0, 0, 0, 0};
 long long g_n[4] = {0, 0, 0, 0};
@@ -74,13 +75,19 @@ void prof_stop(void* token, cudaStream_t st, int cls, double flops) {
 }
 
 void prof_svd(int sweeps, double ms, int kind, int max_rows, double flops, const int* rot_hist, int nhist,
-              int bonds) {
+              int bonds, double alg_flops, double alg_bytes) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_svd_calls += 1;
     g_svd_bonds += bonds;
     g_svd_sweeps += sweeps;
     g_svd_ms += ms;
-    if (kind == 1) g_svd_block += 1, g_svd_block_ms += ms, g_svd_block_flops += flops;
+    if (kind == 1) {
+        g_svd_block += 1;
+        g_svd_block_ms += ms;
+        g_svd_block_flops += flops;
+        g_svd_block_alg_flops += alg_flops;
+        g_svd_block_alg_bytes += alg_bytes;
+    }
     if (kind == 2) g_svd_f64 += 1, g_svd_f64_ms += ms;
     g_svd_rows = std::max<long long>(g_svd_rows, max_rows);
     for (int i = 0; rot_hist && i < nhist && i < 48; ++i) g_rot_hist[i] += rot_hist[i];
@@ -105,6 +112,7 @@ void dmrg_profile_reset(void) {
     for (int i = 0; i < 4; ++i) g_ms[i] = g_fl[i] = 0.0, g_n[i] = 0;
     g_svd_calls = g_svd_sweeps = g_svd_block = g_svd_f64 = g_svd_rows = g_svd_bonds = 0;
     g_svd_ms = g_svd_block_ms = g_svd_f64_ms = g_svd_block_flops = 0.0;
+    g_svd_block_alg_flops = g_svd_block_alg_bytes = 0.0;
     for (auto& x : g_rot_hist) x = 0;
     g_launches.store(0);
     g_fallbacks.store(0);
@@ -150,6 +158,8 @@ dmrg_status dmrg_profile_read(dmrg_profile* out) {
     out->svd_max_rows = g_svd_rows;
     out->svd_fp64_fallbacks = g_fallbacks.load();
     out->svd_block_flops = g_svd_block_flops;
+    out->svd_block_alg_flops = g_svd_block_alg_flops;
+    out->svd_block_alg_bytes = g_svd_block_alg_bytes;
     for (int i = 0; i < 48; ++i) out->svd_rot_hist[i] = g_rot_hist[i];
     out->emu_fallbacks = g_emu_fallbacks.load();
     tune_stats(&out->tune_classes, &out->tune_changed);
