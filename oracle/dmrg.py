@@ -24,6 +24,20 @@ REL_CUTOFF = 1e-12     # discard lambda / lambda_max below this (keeps V = 1/lam
 DEGEN_TOL = 1e-10      # relative gap under which the value at the cut counts as degenerate
 
 
+def thin_svd(M):
+    """M = U diag(S) Vt (thin), S descending -- the SVD of Eq. (svd) as a library step: LAPACK's
+    divide-and-conquer driver, or, where that driver reports non-convergence (it does, rarely, on
+    valid input with some LAPACK builds), the QR-iteration driver, which computes the same
+    factorisation.  Non-finite input is an error, never retried."""
+    if not np.all(np.isfinite(M)):
+        raise FloatingPointError("SVD of a matrix with non-finite entries")
+    try:
+        return np.linalg.svd(M, full_matrices=False)
+    except np.linalg.LinAlgError:
+        import scipy.linalg
+        return scipy.linalg.svd(M, full_matrices=False, lapack_driver="gesvd")
+
+
 # ----------------------------------------------------------------------------------------
 # Projected Hamiltonian (Sec. II): out = sum L[a',w,a] W1[w,s1,s1',w'] W2[w',s2,s2',w''] R[c',w'',c] psi[a,s1',s2',c]
 # ----------------------------------------------------------------------------------------
@@ -222,7 +236,7 @@ def svd_sectors(psi, bl, br, qn, svd=None):
                 if blk is not None:
                     M[r0: r0 + bl[qa], c0: c0 + br[qc]] = blk
         if svd is None:
-            U, S, Vt = np.linalg.svd(M, full_matrices=False)
+            U, S, Vt = thin_svd(M)
         else:
             U, S, Vt = svd(M)
         res[qm] = (U, S, Vt, roff, coff)
@@ -347,7 +361,7 @@ def right_canonicalize(mps_sites, bonds, qn):
             if not cols:
                 continue
             M = np.concatenate([sites[j][(ql, s)] for s, _ in cols], axis=1)
-            U, S, Vt = np.linalg.svd(M, full_matrices=False)
+            U, S, Vt = thin_svd(M)
             k = len(S)
             newdims[ql] = k
             c0 = 0

@@ -202,3 +202,33 @@ def test_sweep_energy_equals_global_expectation():
     assert np.abs(np.delete(v, idx)).max() == 0.0
     psi = D.two_site(eng.sites[0], eng.sites[1], eng.qn)
     assert abs(eng.energy_of(0, psi) - e_full) < 1e-12
+
+
+def test_thin_svd_fallback_driver(monkeypatch):
+    """thin_svd: the SVD of a graded matrix (reconstruction, orthonormal factors, descending
+    values equal to the singular values from the eigenvalues of M^T M); the same when the
+    divide-and-conquer driver reports non-convergence and the QR-iteration driver takes over; a
+    non-finite entry raises instead of being retried."""
+    rng = np.random.default_rng(9)
+    M = rng.standard_normal((40, 25)) * np.logspace(0, -8, 25)[None, :]
+    ref = np.sqrt(np.sort(np.linalg.eigvalsh(M.T @ M))[::-1].clip(0))
+
+    def check(U, S, Vt):
+        assert U.shape == (40, 25) and Vt.shape == (25, 25)
+        assert np.all(np.diff(S) <= 0)
+        assert np.abs((U * S) @ Vt - M).max() <= 1e-13
+        assert np.abs(U.T @ U - np.eye(25)).max() <= 1e-13
+        assert np.abs(Vt @ Vt.T - np.eye(25)).max() <= 1e-13
+        assert np.abs(S[:8] - ref[:8]).max() <= 1e-12 * S[0]   # the well-resolved top of the spectrum
+
+    check(*D.thin_svd(M))
+
+    def fail(*a, **k):
+        raise np.linalg.LinAlgError("SVD did not converge")
+
+    monkeypatch.setattr(np.linalg, "svd", fail)
+    check(*D.thin_svd(M))
+    bad = M.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(FloatingPointError):
+        D.thin_svd(bad)
