@@ -93,3 +93,27 @@ def test_emulation_needs_tensor_cores(lib):
     P = (pd.GemmProblem * 1)(pd.GemmProblem(4, 4, 0, 1, 0, 4, 1, 4, 1, 1, 4, 0, 0, 1.0))
     S = (pd.GemmSegment * 1)(pd.GemmSegment(0, 0, 4, 0))
     assert lib.dmrg_gemm64(P, 1, S, 1, fake, fake, fake, 1, None, None) == 8
+
+
+def test_split_batch_rejects_bad_arguments(lib):
+    """dmrg_svd_split_batch: an empty batch does nothing; a negative count, an unknown mode, a
+    missing array, a null device buffer or m_max < 1 fail before any device access."""
+    import numpy as np
+    import paper_1301_3494_gb300 as pd
+    bond = pd.Bond([1, -1], {0: 1}, {0: 1}, np.zeros((1, 2, 2, 1)), [0], [0])
+    D = (pd.BondDesc * 1)(bond.desc)
+    P = ctypes.c_void_p * 1
+    fake = P(256)                          # never dereferenced: each call fails its checks first
+    mm = (ctypes.c_int * 1)(4)
+    nm = (ctypes.c_int * 1)()
+    qm = (ctypes.c_int * 8)()
+    km = (ctypes.c_int * 8)()
+    f = lib.dmrg_svd_split_batch
+    assert f(0, None, None, None, 0, None, None, None, 0, None, None, None, None, None) == 0
+    assert f(-1, D, fake, mm, 0, fake, fake, fake, 8, nm, qm, km, None, None) == 1
+    for mode in (3, 7, -1):
+        assert f(1, D, fake, mm, mode, fake, fake, fake, 8, nm, qm, km, None, None) == 1, mode
+    assert f(1, D, None, mm, 0, fake, fake, fake, 8, nm, qm, km, None, None) == 1          # no psi array
+    assert f(1, D, P(None), mm, 0, fake, fake, fake, 8, nm, qm, km, None, None) == 1       # null psi buffer
+    assert f(1, D, fake, (ctypes.c_int * 1)(0), 0, fake, fake, fake, 8, nm, qm, km, None, None) == 1
+    assert "m_max" in lib.dmrg_last_error(None).decode()
