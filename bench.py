@@ -451,8 +451,10 @@ def accuracy_leg(args, eng, W, flux, D, qn, sweep_s=None, t_start=None):
     b0, d0, c0 = f64.state()
     t_canon = time.perf_counter() - t0
     if sweep_s is not None and t_start is not None:
-        # the FP64 serial sweep takes ~5x the timed mixed sweep, the mixed one ~1.3x, evaluation ~0.5x
-        projected = time.perf_counter() - t_start + 7.0 * sweep_s
+        # the FP64 serial sweep took ~5x a serial-schedule parallel sweep, the mixed one ~1.3x, evaluation
+        # ~0.5x; the lockstep schedule speeds up the timed sweeps but not these serial ones (measured
+        # together ~340 s at 24x8, m = 2000), so the estimate never drops below that
+        projected = time.perf_counter() - t_start + max(7.0 * sweep_s, 420.0)
         if projected > args.time_budget_s:
             f64.close()
             return {"E_fp64_eval_of_timed_state": e_state, "canonicalise_and_evaluate_s": t_canon,
