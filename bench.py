@@ -670,6 +670,17 @@ def dist_init(args):
     return rank, world, None
 
 
+def max_over_ranks(dist, values, device):
+    """Each value's maximum over all ranks (a job takes as long as its slowest rank); the values
+    themselves on one process."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def main():
     args = parse()
     rank, world, dist = dist_init(args)
@@ -770,10 +781,7 @@ def main():
     pd.profile_enable(False)
     prof = pd.profile_read()
     dev_s = ev0.elapsed_time(ev1) * 1e-3
-    if dist:
-        t = torch.tensor([dev_s, wall], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s, wall = float(t[0]), float(t[1])
+    dev_s, wall = max_over_ranks(dist, [dev_s, wall], "cuda")
     mv_flops = sum(s["matvec_flops"] for s in stats)
     mv_s = sum(s["matvec_seconds"] for s in stats)
     value = world * mv_flops / mv_s / 1e12
