@@ -352,6 +352,9 @@ class Engine:
         _check(lib().dmrg_setup_regions(self._h, int(n_regions), int(warmup), C.byref(p)), self._h)
 
     def sweep(self, m_max, dav_tol=1e-10, dav_max_iter=100, refine_iters=2, serial_regions=0):
+        """One serial sweep, or with regions set up one real-space parallel sweep (Fig. 4).
+        serial_regions: 0 one host thread and stream per region, 1 the regions one after another,
+        2 lockstep (every region's t-th bond step together, their splits in one grouped launch)."""
         p = self.params(m_max, dav_tol, dav_max_iter, refine_iters, serial_regions)
         s = SweepStats()
         _check(lib().dmrg_sweep(self._h, C.byref(p), C.byref(s)), self._h)
