@@ -670,6 +670,65 @@ def dist_init(args):
     return rank, world, None
 
 
+def rooflines(precision, fp64_emulation, prof, rates, pk, pk_kind):
+    """Roofline records of the matvec GEMM (the metric's kernel) and of the block-Jacobi SVD kernel
+    from the library's profile of the timed steps; returns (roofline, roofline_other): the first is
+    whichever of the two took more device time."""
+    if precision == "fp64":
+        g_ms, g_fl, g_n = prof["f64_gemm_ms"], prof["f64_gemm_flops"], prof["f64_gemm_launches"]
+        peak, bound = rates["fp64_fma"], "alu"
+        peak_note = "measured FP64 FMA rate (dmrg_probe kind 0: eight independent DFMA chains per thread)"
+        if fp64_emulation:
+            gemm_kernel = ("k_oz_split + k_tc_gemm (bf16 slices) + k_oz_combine: every FP64 grouped GEMM of the "
+                           "step, emulated")
+            peak_note += ("; emulated GEMMs are counted in FP64-equivalent flops, so frac > 1 is a rate beyond "
+                          "what the FP64 units can deliver")
+        else:
+            gemm_kernel = "k_gemm_simt<double>: every FP64 grouped GEMM of the step"
+    else:
+        gemm_kernel = "k_tc_gemm (matvec L and R stages)"
+        g_ms, g_fl, g_n = prof["mv_gemm_ms"], prof["mv_gemm_flops"], prof["mv_gemm_launches"]
+        peak = pk["bf16_tflops_sustained"] * (1.0 if precision == "bf16" else NOMINAL_TF32_OVER_BF16)
+        bound = "tensor"
+        peak_note = (f"{pk_kind} bf16 sustained" + ("" if precision == "bf16" else " x nominal tf32/bf16"))
+    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    tr = ncu_traffic(f"tc_gemm_matvec_{precision}_traffic") if precision != "fp64" else None
+    roof_mv = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "traffic": tr["bytes_per_launch"] if tr else None, "kernel": gemm_kernel,
+               "launches": g_n, "flops_per_launch": g_fl / max(g_n, 1), "device_ms": g_ms, "peak_source": peak_note}
+    roof = roof_mv
+    if prof["svd_block_calls"] > 0:
+        p32 = rates["fp32_fma"]
+        b_ms, b_fl, b_n = prof["svd_block_ms"], prof["svd_block_flops"], prof["svd_block_calls"]
+        b_alg, b_bytes = prof["svd_block_alg_flops"], prof["svd_block_alg_bytes"]
+        a_alg = b_alg / (b_ms * 1e-3) / 1e12 if b_ms > 0 else 0.0
+        a32 = b_fl / (b_ms * 1e-3) / 1e12 if b_ms > 0 else 0.0
+        # DRAM bytes per algorithmic byte from a small-case capture of the same kernel, times this
+        # run's algorithmic bytes per launch
+        trs = ncu_traffic("bjacobi_queue_traffic")
+        roof_svd = {"bound": "alu", "achieved": a_alg, "peak": p32, "unit": "TFLOP/s", "frac": a_alg / p32,
+                    "traffic": trs["dram_over_algorithmic_bytes"] * b_bytes / b_n if trs else None,
+                    "kernel": "k_bjacobi_queue (FP32 block-Jacobi SVD, one launch per batch of splits)",
+                    "launches": b_n, "flops_per_launch": b_alg / b_n,
+                    "flops_counted": "textbook R-SVD with U and V, 4 p n^2 + 22 n^3 per p x n sector matrix",
+                    "algorithmic_bytes_per_launch": b_bytes / b_n,
+                    "executed_flops_per_launch": b_fl / b_n, "executed_tflops": a32,
+                    "executed_note": "FP32 Gram and rotation flops the Jacobi ran (all its sweeps)",
+                    "traffic_source": (f"dram/algorithmic bytes {trs['dram_over_algorithmic_bytes']:.3f} from "
+                                       f"{trs['source']}" if trs else None),
+                    "device_ms": b_ms,
+                    "peak_source": ("measured FP32 FMA rate (dmrg_probe kind 1: eight independent FFMA chains per "
+                                    f"thread); unit-count rate {fp32_peak_tflops(2070.0):.1f} TFLOP/s at 2070 MHz")}
+        if b_ms > g_ms:
+            roof = roof_svd
+            roof_other = roof_mv
+        else:
+            roof_other = roof_svd
+    else:
+        roof_other = None
+    return roof, roof_other
+
+
 def max_over_ranks(dist, values, device):
     """Each value's maximum over all ranks (a job takes as long as its slowest rank); the values
     themselves on one process."""
@@ -786,63 +845,11 @@ def main():
     mv_s = sum(s["matvec_seconds"] for s in stats)
     value = world * mv_flops / mv_s / 1e12
     ms_step = 1e3 * dev_s / args.steps
-    # roofline of the matvec GEMM (the metric's kernel) and of the block-Jacobi SVD kernel; the
-    # "roofline" key carries whichever of the two took more device time in the timed steps
+    # roofline of the matvec GEMM and of the block-Jacobi SVD kernel
     pk, pk_kind = peaks()
     rates = {"fp64_fma": pd.probe(0), "fp32_fma": pd.probe(1), "bf16_tc_gemm_8192": pd.probe(2),
              "tf32_tc_gemm_8192": pd.probe(3)}
-    if args.precision == "fp64":
-        g_ms, g_fl, g_n = prof["f64_gemm_ms"], prof["f64_gemm_flops"], prof["f64_gemm_launches"]
-        peak, bound = rates["fp64_fma"], "alu"
-        peak_note = "measured FP64 FMA rate (dmrg_probe kind 0: eight independent DFMA chains per thread)"
-        if args.fp64_emulation:
-            gemm_kernel = ("k_oz_split + k_tc_gemm (bf16 slices) + k_oz_combine: every FP64 grouped GEMM of the "
-                           "step, emulated")
-            peak_note += ("; emulated GEMMs are counted in FP64-equivalent flops, so frac > 1 is a rate beyond "
-                          "what the FP64 units can deliver")
-        else:
-            gemm_kernel = "k_gemm_simt<double>: every FP64 grouped GEMM of the step"
-    else:
-        gemm_kernel = "k_tc_gemm (matvec L and R stages)"
-        g_ms, g_fl, g_n = prof["mv_gemm_ms"], prof["mv_gemm_flops"], prof["mv_gemm_launches"]
-        peak = pk["bf16_tflops_sustained"] * (1.0 if args.precision == "bf16" else NOMINAL_TF32_OVER_BF16)
-        bound = "tensor"
-        peak_note = (f"{pk_kind} bf16 sustained" + ("" if args.precision == "bf16" else " x nominal tf32/bf16"))
-    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
-    tr = ncu_traffic(f"tc_gemm_matvec_{args.precision}_traffic") if args.precision != "fp64" else None
-    roof_mv = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-               "traffic": tr["bytes_per_launch"] if tr else None, "kernel": gemm_kernel,
-               "launches": g_n, "flops_per_launch": g_fl / max(g_n, 1), "device_ms": g_ms, "peak_source": peak_note}
-    roof = roof_mv
-    if prof["svd_block_calls"] > 0:
-        p32 = rates["fp32_fma"]
-        b_ms, b_fl, b_n = prof["svd_block_ms"], prof["svd_block_flops"], prof["svd_block_calls"]
-        b_alg, b_bytes = prof["svd_block_alg_flops"], prof["svd_block_alg_bytes"]
-        a_alg = b_alg / (b_ms * 1e-3) / 1e12 if b_ms > 0 else 0.0
-        a32 = b_fl / (b_ms * 1e-3) / 1e12 if b_ms > 0 else 0.0
-        # DRAM bytes per algorithmic byte from a small-case capture of the same kernel, times this
-        # run's algorithmic bytes per launch
-        trs = ncu_traffic("bjacobi_queue_traffic")
-        roof_svd = {"bound": "alu", "achieved": a_alg, "peak": p32, "unit": "TFLOP/s", "frac": a_alg / p32,
-                    "traffic": trs["dram_over_algorithmic_bytes"] * b_bytes / b_n if trs else None,
-                    "kernel": "k_bjacobi_queue (FP32 block-Jacobi SVD, one launch per batch of splits)",
-                    "launches": b_n, "flops_per_launch": b_alg / b_n,
-                    "flops_counted": "textbook R-SVD with U and V, 4 p n^2 + 22 n^3 per p x n sector matrix",
-                    "algorithmic_bytes_per_launch": b_bytes / b_n,
-                    "executed_flops_per_launch": b_fl / b_n, "executed_tflops": a32,
-                    "executed_note": "FP32 Gram and rotation flops the Jacobi ran (all its sweeps)",
-                    "traffic_source": (f"dram/algorithmic bytes {trs['dram_over_algorithmic_bytes']:.3f} from "
-                                       f"{trs['source']}" if trs else None),
-                    "device_ms": b_ms,
-                    "peak_source": ("measured FP32 FMA rate (dmrg_probe kind 1: eight independent FFMA chains per "
-                                    f"thread); unit-count rate {fp32_peak_tflops(2070.0):.1f} TFLOP/s at 2070 MHz")}
-        if b_ms > g_ms:
-            roof = roof_svd
-            roof_other = roof_mv
-        else:
-            roof_other = roof_svd
-    else:
-        roof_other = None
+    roof, roof_other = rooflines(args.precision, args.fp64_emulation, prof, rates, pk, pk_kind)
     e2e_value = world * mv_flops / wall / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
