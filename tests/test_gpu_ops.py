@@ -227,9 +227,9 @@ def test_svd_split_batch_equals_single_splits(mode):
     bond, what dmrg_svd_split returns for that bond alone -- same block table, discarded weight,
     lambda and factors -- and what the oracle returns: FP64 mode (0) to 1e-12; the FP32 block
     Jacobi (2, and 6 without the QR) to the FP32 split's bounds (lambda 1e-4 lambda_max, the
-    reconstruction 2e-4 normwise), lambda to 1e-5 lambda_max of the single-bond FP32 run
-    (thresholds are per sector; the staging of a sector's columns, and so the rounding of its
-    rotations, follows the batch's largest sector)."""
+    reconstruction 2e-4 normwise), lambda to 5e-5 lambda_max of the single-bond FP32 run (the
+    FP32 Jacobi stops at a relative off-diagonal of 3e-5, and the staging of a sector's columns,
+    so the rounding of its rotations, follows the batch's largest sector)."""
     cases = [("chain", 200, 120), ("cyl", 420, 300), ("tfim", 80, 50), ("chain", 12, 6)]
     fp32 = (mode & 3) == 2
     bonds, xs, single, batch, refs, mmaxs = [], [], [], [], [], []
@@ -273,7 +273,7 @@ def test_svd_split_batch_equals_single_splits(mode):
         lam_s = s_bufs[1].cpu().numpy()[:kept]
         lam_ref = np.concatenate([lam[q] for q in sorted(lam)]) if not fp32 else None
         if fp32:
-            assert np.abs(lam_b - lam_s).max() <= 1e-5 * spec[0]
+            assert np.abs(lam_b - lam_s).max() <= 5e-5 * spec[0]
             got = np.sort(lam_b)[::-1]
             assert np.abs(got - spec[:kept] / np.sqrt((spec[:kept] ** 2).sum())).max() <= 1e-4 * spec[0]
             assert abs(tr_b - tr_s) <= 1e-5
